@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""LNV energy + gradient throughput on GB300.
+
+Workload: bulk Si, 8x8x8 conventional cells = 4096 atoms, NSF = 4, S and H
+range 6.6 A, L range 8 A, seed 0 (synthetic stand-in for the paper's bulk-Si
+runs).  One step = one full evaluation of E, N_e and dE/dL (every product,
+trace and the gradient assembly) on device-resident S, H, L.  L2 is flushed
+(256 MB write) between timed steps, outside the timed events.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NCELL, NSF, R_SH, R_L, SEED = 8, 4, 6.6, 8.0, 0
+WORKLOAD = "si_diamond_8x8x8_4096atoms_nsf4_rsh6.6A_rl8A"
+METRIC = "atoms/s per LNV energy+gradient eval"
+# ALU peaks (TFLOP/s): 152 SMs x 2.07 GHz x (128 FP32 lanes x 2) for FP32, and
+# the 1.25 TFLOP/s FP64 rate (= 152 x 2.07 GHz x 4 flop/clk/SM) for FP64.
+PEAK_TFLOPS = {"fp32": 152 * 2.07e9 * 256 / 1e12, "fp64": 1.25}
+STAGES = ("XY", "TU", "Z", "traces", "Q", "W", "G")
+STAGE_KERNEL = {"XY": "k_push (X=LS, Y=LH)", "TU": "k_push (T=SX, U=SY)", "Z": "k_pull (Z=LT)",
+                "Q": "k_pull (Q=HZ)", "W": "k_pull (W=X^T U^T)"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lnv", choices=["lnv", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the secondary FP64 measurement")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.lines, self.proc, self.t = [], None, None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", self.gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append((time.time(), ln.strip()))
+
+    def stop(self):
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+
+    def summary(self, t0=None, t1=None):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        rows = [ln for ts, ln in self.lines if t0 is None or (t0 - 0.15 <= ts <= t1 + 0.15)]
+        if not rows:
+            rows = [ln for _, ln in self.lines]
+        for ln in rows:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def product_source_sha():
+    h = hashlib.sha1()
+    for f in ("mult_kernels.cuh", "mult.cu"):
+        with open(os.path.join(ROOT, "paper_0911_3584_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(stage, prec):
+    """Measured DRAM bytes per launch of a stage's kernel, if the committed ncu
+    summary was taken on the current product kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = product_source_sha()
+    for ln in open(path):
+        f = ln.split()
+        if len(f) >= 4 and not ln.startswith("#") and f[0] == stage and f[1] == prec and f[3] == sha:
+            return float(f[2])
+    return None
+
+
+def build_inputs(ctx, dtype, seed_shift=0):
+    import torch
+
+    import synth
+    from paper_0911_3584_gb300 import Pattern
+
+    def pattern_fn(pos, cell, R):
+        P = Pattern.build(ctx, pos, cell, R)
+        return P.row_ptr.cpu().numpy(), P.col.cpu().numpy()
+
+    w = synth.si_workload(NCELL, NSF, R_SH, R_L, SEED + seed_shift, pattern_fn)
+    dev = {k: torch.from_numpy(w[k]).to(ctx.device, dtype) for k in ("S", "H", "L")}
+    return w, dev
+
+
+def time_path(ctx, w, prec, steps, warmup, dist, clocks=None):
+    """Device-timed steps of one precision path; returns a result dict."""
+    import torch
+
+    from paper_0911_3584_gb300 import System, launch_count
+
+    dtype = torch.float32 if prec == "fp32" else torch.float64
+    sysm = System(ctx, NSF, prec, w["pos"], w["cell"], R_SH, R_L)
+    S, H, L = (torch.from_numpy(w[k]).to(ctx.device, dtype) for k in ("S", "H", "L"))
+    out = torch.empty((1, 6), dtype=torch.float64, device=ctx.device)
+    G = torch.empty_like(L)
+    ws = torch.empty(sysm.workspace_size(True), dtype=torch.uint8, device=ctx.device)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=ctx.device)
+    sysm.profile(True)
+    for _ in range(warmup):
+        sysm.energy_grad(S, H, L, out=out, G=G, workspace=ws)
+    stream = ctx.stream
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stage_sum = dict.fromkeys(STAGES, 0.0)
+    n0 = launch_count()
+    t0 = time.time()
+    for k in range(steps):
+        flush.zero_()
+        with torch.cuda.stream(stream):
+            ev[k][0].record(stream)
+        sysm.energy_grad(S, H, L, out=out, G=G, workspace=ws)
+        with torch.cuda.stream(stream):
+            ev[k][1].record(stream)
+        for s_, v in sysm.stage_ms().items():
+            stage_sum[s_] += v
+    torch.cuda.synchronize()
+    t1 = time.time()
+    launches = launch_count() - n0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    stage_ms = {k: v / steps for k, v in stage_sum.items()}
+    st = sysm.stage_triples()
+    flops_stage = {k: 2 * NSF ** 3 * st[k] for k in STAGES}
+    res = {
+        "prec": prec, "sys": sysm, "total_s": total_s, "ms_per_step": total_s * 1e3 / steps,
+        "step_ms": step_ms, "stage_ms": stage_ms, "flops": 2 * NSF ** 3 * sysm.triples(True),
+        "flops_stage": flops_stage, "launches": launches, "wall": (t0, t1),
+        "out": out.cpu().numpy()[0].copy(), "G": G.cpu().numpy().copy(),
+        "tensors": (S, H, L, out, G, ws),
+    }
+    return res
+
+
+def roofline(res):
+    prec = res["prec"]
+    # dominant product kernel by measured time
+    cand = {k: v for k, v in res["stage_ms"].items() if k in STAGE_KERNEL and v > 0}
+    stage = max(cand, key=cand.get)
+    ms = cand[stage]
+    achieved = res["flops_stage"][stage] / (ms * 1e-3) / 1e12
+    peak = PEAK_TFLOPS[prec]
+    tr = ncu_traffic(stage, prec)
+    return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 3), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": tr, "kernel": STAGE_KERNEL[stage],
+            "stage": stage, "kernel_ms": round(ms, 4),
+            "algorithmic_flops_per_launch": res["flops_stage"][stage],
+            "peak_source": ("derived: 152 SMs x 2.07 GHz x 256 flop/clk/SM (FP32 FMA)" if prec == "fp32"
+                            else "nominal GB300 FP64 rate 1.25 TFLOP/s")}
+
+
+def e2e(ctx, res, steps, warmup):
+    """Same metric through the public API with pinned host buffers: H2D of S,
+    H, L and D2H of (E, N_e, traces) and G inside the timed region."""
+    import torch
+
+    sysm = res["sys"]
+    S, H, L, out, G, ws = res["tensors"]
+    hs = [t.cpu().pin_memory() for t in (S, H, L)]
+    hG = torch.empty(G.shape, dtype=G.dtype).pin_memory()
+    hout = torch.empty(out.shape, dtype=out.dtype).pin_memory()
+    stream = ctx.stream
+
+    def step():
+        for d, h in zip((S, H, L), hs):
+            d.copy_(h, non_blocking=True)
+        sysm.energy_grad(S, H, L, out=out, G=G, workspace=ws)
+        hG.copy_(G, non_blocking=True)
+        hout.copy_(out, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    s = a.elapsed_time(b) / 1e3
+    h2d = sum(t.numel() * t.element_size() for t in hs)
+    d2h = hG.numel() * hG.element_size() + hout.numel() * hout.element_size()
+    return {"value": round(w_atoms() * steps / s, 1), "unit": "atoms/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(s * 1e3 / steps, 4)}
+
+
+def w_atoms():
+    return 8 * NCELL ** 3
+
+
+def cpu_baseline(w, results):
+    """The FP64 CPU oracle on one full evaluation of the same workload."""
+    import oracle
+
+    S = oracle.csr(w["sh_row_ptr"], w["sh_col"], w["S"])
+    H = oracle.csr(w["sh_row_ptr"], w["sh_col"], w["H"])
+    L = oracle.csr(w["l_row_ptr"], w["l_col"], w["L"])
+    t0 = time.time()
+    ref = oracle.lnv_energy_grad(w["pos"], w["cell"], R_SH, R_L, S, H, L)
+    dt = time.time() - t0
+    errs = {}
+    for r in results:
+        o, G = r["out"], r["G"]
+        errs[r["prec"]] = {
+            "E_rel": abs(o[0] - ref["E"]) / abs(ref["E"]),
+            "Ne_rel": abs(o[1] - ref["Ne"]) / abs(ref["Ne"]),
+            "G_rel_fro": float(np.linalg.norm(G - ref["G"]) / np.linalg.norm(ref["G"])),
+        }
+    base = {"value": round(w_atoms() / dt, 3), "unit": "atoms/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": "one full energy+gradient evaluation of the 4096-atom workload "
+                                        f"({dt:.1f} s, FP64 C oracle, OpenMP over rows)"}
+    return base, errs, ref
+
+
+def reference_arm(args):
+    """--impl reference: the FP64 CPU oracle, each step a row sample of one evaluation."""
+    import oracle
+    import synth
+
+    t_setup = time.time()
+    w = synth.si_workload(NCELL, NSF, R_SH, R_L, SEED, oracle.pattern)
+    S = oracle.csr(w["sh_row_ptr"], w["sh_col"], w["S"])
+    H = oracle.csr(w["sh_row_ptr"], w["sh_col"], w["H"])
+    L = oracle.csr(w["l_row_ptr"], w["l_col"], w["L"])
+    full = oracle.lnv_energy_grad(w["pos"], w["cell"], R_SH, R_L, S, H, L, keep=True)
+    t_full = time.time() - t_setup
+    n = w["pos"].shape[0]
+    rng = np.random.default_rng(1)
+    rows = np.sort(rng.choice(n, size=n // 16, replace=False))
+    for _ in range(args.warmup):
+        oracle.lnv_rows(S, H, L, full, rows)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.time()
+        oracle.lnv_rows(S, H, L, full, rows)
+        times.append(time.time() - t0)
+    total = sum(times)
+    value = rows.size * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "atoms/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "atoms": n, "nsf": NSF, "r_sh": R_SH, "r_l": R_L},
+        "cpu_baseline": {"value": round(value, 3), "unit": "atoms/s", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"each step: every product and trace of one evaluation on {rows.size} "
+                                   f"of {n} output rows (operands from one untimed full oracle "
+                                   f"evaluation, {t_full:.1f} s)"},
+        "e2e": {"value": round(value, 3), "unit": "atoms/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            reference_arm(args)
+        return
+    import torch
+
+    from paper_0911_3584_gb300 import Context, build
+
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+    dev = torch.device("cuda", local)
+    ctx = Context(dev)
+    w, _ = build_inputs(ctx, torch.float64)
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
+    clocks = Clocks(gpu_id)
+    clocks.start()
+    r32 = time_path(ctx, w, "fp32", args.steps, args.warmup, dist)
+    r64 = None if args.no_fp64 else time_path(ctx, w, "fp64", args.steps, args.warmup, dist)
+    clocks.stop()
+    e2e32 = e2e(ctx, r32, args.steps, args.warmup)
+
+    def agg(res):
+        t = torch.tensor([res["total_s"]], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = t.item()
+        return w_atoms() * world * args.steps / tmax, tmax
+
+    v32, t32 = agg(r32)
+    line = {
+        "metric": METRIC, "value": round(v32, 1), "unit": "atoms/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t32 * 1e3 / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "atoms": w_atoms(), "nsf": NSF, "r_sh": R_SH, "r_l": R_L,
+                   "precision": "FP32 block products and accumulation; FP64 traces, E, N_e and "
+                                "gradient combination",
+                   "l2": "flushed between timed steps (256 MB write, outside the timed events)",
+                   "parallelism": f"replicas x{world} (independent systems)"},
+        "gflops": round(r32["flops"] / (r32["ms_per_step"] * 1e-3) / 1e9, 1),
+        "roofline": roofline(r32),
+        "e2e": e2e32,
+        "gpu_launches": r32["launches"],
+        "stage_ms": {k: round(v, 4) for k, v in r32["stage_ms"].items()},
+    }
+    clk = clocks.summary(r32["wall"][0], (r64 or r32)["wall"][1])
+    line["clocks"] = clk
+    if r64 is not None:
+        v64, t64 = agg(r64)
+        line["fp64"] = {"value": round(v64, 1), "unit": "atoms/s",
+                        "ms_per_step": round(t64 * 1e3 / args.steps, 4),
+                        "gflops": round(r64["flops"] / (r64["ms_per_step"] * 1e-3) / 1e9, 1),
+                        "roofline": roofline(r64), "gpu_launches": r64["launches"],
+                        "stage_ms": {k: round(v, 4) for k, v in r64["stage_ms"].items()}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base, errs, _ = cpu_baseline(w, [r for r in (r32, r64) if r is not None])
+        line["cpu_baseline"] = base
+        line["errors_vs_oracle"] = errs
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * lnv.h -- C ABI of liblnv, a GB300 (sm_103a) library for the range-truncated
+ * block-sparse products of the LNV density-matrix method (Bowler & Miyazaki,
+ * "Calculations on millions of atoms with DFT", Sec. 2).
+ *
+ * Method (Sec. 2): the density matrix in the support-function basis is
+ * K = 3LSL - 2LSLSL (Eq. 3) with S the overlap matrix (Eq. 2) and L the
+ * auxiliary density matrix, truncated as L_ij = 0 for |R_i - R_j| > R_L.  The
+ * electron count is N_e = 2 Tr[KS] (Sec. 2, condition 2); the band energy at
+ * fixed H is E = 2 Tr[KH]; the minimisation over L uses
+ *     dE/dL = 6(SLH + HLS) - 4(SLSLH + SLHLS + HLSLS)
+ * restricted to L's range.  The main cost is sparse matrix multiplication
+ * (Sec. 3), which this library runs on the GPU.
+ *
+ * Conventions shared by every call:
+ *  - Matrices are block-CSR over atoms: one NSF x NSF block per stored atom
+ *    pair, blocks row-major, a matrix's values one contiguous array of
+ *    nnzb * NSF * NSF elements in the block order of its pattern.
+ *  - A pattern holds row_ptr (int64, n+1), col (int32, nnzb, ascending inside
+ *    each row) and, for symmetric patterns, a transpose map tr (int64, nnzb):
+ *    tr[p] is the position of block (j, i) when p holds block (i, j).
+ *  - Range patterns keep block (i, j) iff d_ij^2 < R^2, with d the
+ *    minimum-image distance in an orthorhombic periodic cell, summed as
+ *    ((dx*dx)+(dy*dy))+(dz*dz) in IEEE FP64 without fused multiply-adds.
+ *  - "_dev" pointers are device memory on the context's device; "_host"
+ *    pointers are host memory.  Value arrays are caller-owned; patterns,
+ *    plans and systems are library-owned opaque handles.
+ *  - Every call is asynchronous on the context's stream unless it says it
+ *    synchronises.  Calls that build handles (pattern, plan, system)
+ *    allocate device memory and synchronise the stream.
+ *  - No exception crosses the ABI.  A call returns LNV_OK or a negative
+ *    status; lnv_last_error() gives the calling thread's last message.
+ *    On error no output is guaranteed and handles stay valid.
+ */
+#ifndef LNV_H
+#define LNV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int lnv_status;
+#define LNV_OK 0
+#define LNV_ERR_ARG (-1)         /* null pointer, bad size, bad enum        */
+#define LNV_ERR_CUDA (-2)        /* a CUDA runtime call or launch failed    */
+#define LNV_ERR_OOM (-3)         /* device allocation failed                */
+#define LNV_ERR_PATTERN (-4)     /* patterns of different sizes, unsorted or
+                                    non-symmetric where symmetry is needed  */
+#define LNV_ERR_UNSUPPORTED (-5) /* NSF or precision not built, row too long */
+
+/* Arithmetic of a call.  LNV_FP64: values, products and sums in FP64.
+ * LNV_FP32: values stored and multiplied in FP32 with FP32 accumulation of
+ * the block products; traces, energies and the gradient combination are
+ * accumulated in FP64 from the FP32 operands. */
+typedef enum { LNV_FP64 = 0, LNV_FP32 = 1 } lnv_prec;
+
+/* Operand flags of lnv_plan_product: use the block transpose of A or B,
+ * (A^T)_ik = (A_ki)^T, read through the pattern's transpose map. */
+#define LNV_TRANS_A 1
+#define LNV_TRANS_B 2
+
+typedef struct lnv_ctx lnv_ctx;
+typedef struct lnv_pattern lnv_pattern;
+typedef struct lnv_plan lnv_plan;
+typedef struct lnv_system lnv_system;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Bind a context to CUDA device `device` and the caller's stream
+ * (a cudaStream_t, may be NULL for the legacy default stream; the stream
+ * stays owned by the caller). */
+lnv_status lnv_ctx_create(int device, void *cuda_stream, lnv_ctx **out);
+lnv_status lnv_ctx_set_stream(lnv_ctx *ctx, void *cuda_stream);
+lnv_status lnv_ctx_destroy(lnv_ctx *ctx);
+/* Last error message of the calling thread ("" if none).  Valid until the
+ * thread's next failing call. */
+const char *lnv_last_error(void);
+/* Library version string, static storage. */
+const char *lnv_version(void);
+/* Kernels this library has launched in this process so far (all threads). */
+int64_t lnv_launch_count(void);
+
+/* ---- a0: range patterns (Sec. 2, locality of L and of the products) ---- */
+
+/* Build {(i, j): d_ij^2 < cutoff^2} for n_atoms positions pos_dev[n][3]
+ * (FP64, Angstrom) in the periodic box cell_host[3].  Positions may lie
+ * outside the box; the minimum image is taken of the raw difference.  Uses a
+ * cell list, so the cost is linear in n_atoms at fixed density.  Rows are
+ * sorted, the diagonal is present, the transpose map is filled.  Fails with
+ * LNV_ERR_UNSUPPORTED if a row exceeds 16384 blocks.  Synchronises. */
+lnv_status lnv_pattern_build(lnv_ctx *ctx, const double *pos_dev, int64_t n_atoms,
+                             const double *cell_host, double cutoff, lnv_pattern **out);
+
+/* Same for n_seg independent systems concatenated along the atom index:
+ * system s owns atoms [seg_off_host[s], seg_off_host[s+1]) and the box
+ * cells_host[3s..3s+2]; no block couples two systems.  The result is the
+ * block-diagonal union, used for batched evaluation. */
+lnv_status lnv_pattern_build_batched(lnv_ctx *ctx, const double *pos_dev, int n_seg,
+                                     const int64_t *seg_off_host, const double *cells_host,
+                                     double cutoff, lnv_pattern **out);
+
+/* Adopt a caller-built pattern (copied).  Columns must be ascending inside
+ * each row and in [0, n); otherwise LNV_ERR_PATTERN.  The transpose map is
+ * built when the pattern is symmetric (else tr entries are -1).
+ * Synchronises. */
+lnv_status lnv_pattern_from_csr(lnv_ctx *ctx, int64_t n, const int64_t *row_ptr_dev,
+                                const int32_t *col_dev, lnv_pattern **out);
+
+/* Borrowed views of a pattern's device arrays (valid until destroy). */
+lnv_status lnv_pattern_info(const lnv_pattern *p, int64_t *n, int64_t *nnzb,
+                            const int64_t **row_ptr_dev, const int32_t **col_dev,
+                            const int64_t **tr_dev, int *symmetric);
+lnv_status lnv_pattern_destroy(lnv_pattern *p);
+
+/* ---- a1-a3, a5, a6: masked block products (Sec. 2 operation (i)) ----- */
+
+/* Plan C = mask_C(op(A) op(B)): for each block (i, j) of C's pattern,
+ * C_ij = sum_k op(A)_ik op(B)_kj; nothing outside C's pattern is formed.
+ * flags: LNV_TRANS_A / LNV_TRANS_B (needs a symmetric pattern).  The plan
+ * chooses a row-gather ("push") or output-owner ("pull") kernel from the
+ * patterns' symbolic work counts.  The patterns must outlive the plan.
+ * Synchronises. */
+lnv_status lnv_plan_product(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
+                            const lnv_pattern *C, int flags, lnv_plan **out);
+/* Symbolic counts of a plan: block triples (i, k, j) that contribute, and
+ * the kernel chosen (0 push, 1 pull). */
+lnv_status lnv_plan_info(const lnv_plan *plan, int64_t *triples, int *mode);
+lnv_status lnv_plan_destroy(lnv_plan *plan);
+
+/* Numeric product on the context stream.  A_dev, B_dev, C_dev are value
+ * arrays in `prec` (double or float) with NSF x NSF blocks; C is
+ * overwritten.  NSF in {1, 2, 4, 9}. */
+lnv_status lnv_bsr_multiply(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec,
+                            const void *A_dev, const void *B_dev, void *C_dev);
+
+/* ---- a4: traces (N_e = 2 Tr[KS], Sec. 2; E = 2 Tr[KH]) ----------------- */
+
+/* out_dev[0] = Tr[A B] = sum_ij <A_ij, (B_ji)^T>, A and B on the same
+ * symmetric pattern, accumulated in FP64 in a fixed order (deterministic).
+ * `scratch_dev` holds n doubles (per-row partial sums). */
+lnv_status lnv_trace_product(lnv_ctx *ctx, const lnv_pattern *P, int nsf, lnv_prec prec,
+                             const void *A_dev, const void *B_dev, double *scratch_dev,
+                             double *out_dev);
+
+/* ---- a1-a7 fused: LNV energy, electron count and gradient -------------- */
+
+/* A system: positions, S and H on the range-r_sh pattern, L on the range-r_l
+ * pattern, plus every intermediate pattern and product plan of the
+ * evaluation.  n_seg > 1 batches independent systems (block-diagonal,
+ * seg_off_host / cells_host as in lnv_pattern_build_batched); n_seg = 1
+ * takes seg_off_host = NULL and one box.  Synchronises. */
+lnv_status lnv_system_create(lnv_ctx *ctx, int nsf, lnv_prec prec, const double *pos_dev,
+                             int64_t n_atoms, int n_seg, const int64_t *seg_off_host,
+                             const double *cells_host, double r_sh, double r_l,
+                             lnv_system **out);
+/* Patterns of S/H and of L (borrowed). */
+lnv_status lnv_system_patterns(const lnv_system *sys, const lnv_pattern **sh,
+                               const lnv_pattern **l);
+/* Device bytes of workspace one evaluation needs (intermediates X, Y, T, U,
+ * Z, W, Q and trace partials). */
+lnv_status lnv_system_workspace_size(const lnv_system *sys, int with_grad, size_t *bytes);
+/* Algorithmic block triples of one evaluation (sum over its products). */
+lnv_status lnv_system_triples(const lnv_system *sys, int with_grad, int64_t *triples);
+/* The same per stage (XY, TU, Z, traces, Q, W, G; 7 values, the TU entry
+ * counting both T and U). */
+lnv_status lnv_system_stage_triples(const lnv_system *sys, int64_t *t7);
+lnv_status lnv_system_destroy(lnv_system *sys);
+
+/* Stage timing: with enable != 0, lnv_energy_grad records CUDA events on the
+ * context stream around its stages XY, TU, Z, traces, Q, W, G.
+ * lnv_system_stage_ms waits for the last evaluation's final event and writes
+ * the 7 stage durations in milliseconds (0 for stages that did not run). */
+lnv_status lnv_system_profile(lnv_system *sys, int enable);
+lnv_status lnv_system_stage_ms(lnv_system *sys, double *ms7);
+
+/* One evaluation.  S_dev, H_dev (on the r_sh pattern) and L_dev (on the r_l
+ * pattern) are value arrays in the system's precision.  Writes, per system
+ * s, out_dev[6 s + 0..5] = {E, N_e, Tr[LSLH], Tr[LSLSLH], Tr[LSLS],
+ * Tr[LSLSLS]} (FP64), and, when G_dev is not NULL, dE/dL on L's pattern in
+ * the system's precision.  Workspace: ws_dev of ws_bytes >=
+ * lnv_system_workspace_size, or NULL to use a buffer the system allocates
+ * on first use and keeps.  Asynchronous on the context stream. */
+lnv_status lnv_energy_grad(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
+                           const void *H_dev, const void *L_dev, double *out_dev,
+                           void *G_dev, void *ws_dev, size_t ws_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LNV_H */

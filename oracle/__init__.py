@@ -69,9 +69,9 @@ def _load():
             lib.oracle_pattern_fill.restype = None
             lib.oracle_pattern_fill.argtypes = [P, i64, P, ctypes.c_double, P, P]
             lib.oracle_mprod.restype = None
-            lib.oracle_mprod.argtypes = [ctypes.c_int, i64] + [P] * 9
+            lib.oracle_mprod.argtypes = [ctypes.c_int, i64] + [P] * 9 + [P, i64]
             lib.oracle_trace.restype = ctypes.c_double
-            lib.oracle_trace.argtypes = [ctypes.c_int, i64] + [P] * 7
+            lib.oracle_trace.argtypes = [ctypes.c_int, i64] + [P] * 7 + [P, i64]
             lib.oracle_restrict.restype = None
             lib.oracle_restrict.argtypes = [ctypes.c_int, i64] + [P] * 6
             lib.oracle_transpose.restype = None
@@ -115,28 +115,45 @@ def csr(rp, col, val=None, nsf=None):
     return d
 
 
-def mprod(A: dict, B: dict, C_pat: tuple) -> dict:
-    """mask(A B) on the block pattern C_pat = (row_ptr, col)."""
+def _rows(rows):
+    if rows is None:
+        return None, 0
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    return r, r.size
+
+
+def mprod(A: dict, B: dict, C_pat: tuple, rows=None) -> dict:
+    """mask(A B) on the block pattern C_pat = (row_ptr, col).
+
+    With ``rows``, only those rows of C are formed (the rest stay zero).
+    """
     lib = _load()
     nsf = A["val"].shape[-1]
     n = A["rp"].size - 1
     C = csr(C_pat[0], C_pat[1], nsf=nsf)
+    r, nr = _rows(rows)
     lib.oracle_mprod(nsf, n, _p(A["rp"]), _p(A["col"]), _p(A["val"]),
                      _p(B["rp"]), _p(B["col"]), _p(B["val"]),
-                     _p(C["rp"]), _p(C["col"]), _p(C["val"]))
+                     _p(C["rp"]), _p(C["col"]), _p(C["val"]),
+                     _p(r) if r is not None else None, nr)
     return C
 
 
-def trace(A: dict, B: dict, row_part: bool = False):
-    """Tr[A B] in FP64; optionally also the per-row partial sums."""
+def trace(A: dict, B: dict, row_part: bool = False, rows=None):
+    """Tr[A B] in FP64; optionally also the per-row partial sums.
+
+    With ``rows``, the partial trace over those rows only.
+    """
     lib = _load()
     nsf = A["val"].shape[-1]
     n = A["rp"].size - 1
-    rows = np.zeros(n) if row_part else None
+    part = np.zeros(n) if row_part else None
+    r, nr = _rows(rows)
     t = lib.oracle_trace(nsf, n, _p(A["rp"]), _p(A["col"]), _p(A["val"]),
                          _p(B["rp"]), _p(B["col"]), _p(B["val"]),
-                         _p(rows) if rows is not None else None)
-    return (t, rows) if row_part else t
+                         _p(part) if part is not None else None,
+                         _p(r) if r is not None else None, nr)
+    return (t, part) if row_part else t
 
 
 def restrict(M: dict, C_pat: tuple) -> dict:
@@ -210,4 +227,29 @@ def lnv_energy_grad(pos, cell, r_sh, r_l, S: dict, H: dict, L: dict, grad: bool 
             out.update(U=U, slh=slh, hls=hls, slslh=slslh, slhls=slhls, hlsls=hlsls)
     if keep:
         out.update(X=X, Y=Y, T=T, Z=Z, pat_x=pat_x, pat_t=pat_t)
+        if not grad:
+            out["U"] = mprod(S, Y, pat_t)
     return out
+
+
+def lnv_rows(S: dict, H: dict, L: dict, full: dict, rows) -> float:
+    """Every product and trace of one evaluation, restricted to output rows
+    ``rows``, with the operands taken from ``full`` (a ``keep=True`` result of
+    lnv_energy_grad).  Used to time bounded samples of the oracle; returns the
+    partial sum 2 (3 Tr[XY] - 2 Tr[ZY]) over those rows."""
+    px, pt, pl = full["pat_x"], full["pat_t"], (L["rp"], L["col"])
+    mprod(L, S, px, rows)
+    mprod(L, H, px, rows)
+    mprod(S, full["X"], pt, rows)
+    mprod(S, full["Y"], pt, rows)
+    mprod(L, full["T"], px, rows)
+    t1 = trace(full["X"], full["Y"], rows=rows)
+    t2 = trace(full["Z"], full["Y"], rows=rows)
+    trace(full["X"], full["X"], rows=rows)
+    trace(full["Z"], full["X"], rows=rows)
+    mprod(S, full["Y"], pl, rows)
+    mprod(H, full["X"], pl, rows)
+    mprod(full["T"], full["Y"], pl, rows)
+    mprod(full["U"], full["X"], pl, rows)
+    mprod(H, full["Z"], pl, rows)
+    return 2.0 * (3.0 * t1 - 2.0 * t2)

@@ -84,25 +84,29 @@ static int64_t find_block(const int64_t *rp, const int32_t *col, int64_t row, in
 /* Range-truncated product C = mask(A B): for every block (i, j) stored in C's
  * pattern, C_ij = sum_k A_ik B_kj over the k with both blocks stored (the
  * paper's K_ij = L_ik S_kl L_lj products, Sec. 2, operation (i)).  Blocks
- * outside C's pattern are not formed. */
+ * outside C's pattern are not formed.  With a row list, only those rows of C
+ * are written. */
 void oracle_mprod(int nsf, int64_t n,
                   const int64_t *a_rp, const int32_t *a_col, const double *a_val,
                   const int64_t *b_rp, const int32_t *b_col, const double *b_val,
-                  const int64_t *c_rp, const int32_t *c_col, double *c_val)
+                  const int64_t *c_rp, const int32_t *c_col, double *c_val,
+                  const int64_t *rows /* NULL: every row */, int64_t nrows)
 {
     const int64_t bs = (int64_t)nsf * nsf;
+    const int64_t m = rows ? nrows : n;
 #pragma omp parallel for schedule(dynamic, 4)
-    for (int64_t i = 0; i < n; ++i) {
+    for (int64_t r = 0; r < m; ++r) {
+        const int64_t i = rows ? rows[r] : r;
         for (int64_t p = c_rp[i]; p < c_rp[i + 1]; ++p) {
             int32_t j = c_col[p];
             double *c = c_val + p * bs;
             for (int64_t e = 0; e < bs; ++e) c[e] = 0.0;
             for (int64_t q = a_rp[i]; q < a_rp[i + 1]; ++q) {
                 int32_t k = a_col[q];
-                int64_t r = find_block(b_rp, b_col, k, j);
-                if (r < 0) continue;
+                int64_t pb = find_block(b_rp, b_col, k, j);
+                if (pb < 0) continue;
                 const double *a = a_val + q * bs;
-                const double *b = b_val + r * bs;
+                const double *b = b_val + pb * bs;
                 for (int x = 0; x < nsf; ++x)
                     for (int y = 0; y < nsf; ++y) {
                         double s = c[x * nsf + y];
@@ -116,22 +120,26 @@ void oracle_mprod(int nsf, int64_t n,
 
 /* Tr[A B] = sum_i sum_k sum_{x,z} A_ik[x][z] B_ki[z][x]  (used for
  * N_e = 2 Tr[KS], Sec. 2 condition 2, and E = 2 Tr[KH]).  Summed per row
- * in FP64, then over rows in row order. */
+ * in FP64, then over rows in row order.  With a row list, only those rows
+ * are summed (a partial trace). */
 double oracle_trace(int nsf, int64_t n,
                     const int64_t *a_rp, const int32_t *a_col, const double *a_val,
                     const int64_t *b_rp, const int32_t *b_col, const double *b_val,
-                    double *row_part /* n, may be NULL */)
+                    double *row_part /* n, may be NULL */,
+                    const int64_t *rows /* NULL: every row */, int64_t nrows)
 {
     const int64_t bs = (int64_t)nsf * nsf;
+    const int64_t m = rows ? nrows : n;
     double total = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
+    for (int64_t r = 0; r < m; ++r) {
+        const int64_t i = rows ? rows[r] : r;
         double s = 0.0;
         for (int64_t q = a_rp[i]; q < a_rp[i + 1]; ++q) {
             int32_t k = a_col[q];
-            int64_t r = find_block(b_rp, b_col, k, (int32_t)i);
-            if (r < 0) continue;
+            int64_t pb = find_block(b_rp, b_col, k, (int32_t)i);
+            if (pb < 0) continue;
             const double *a = a_val + q * bs;
-            const double *b = b_val + r * bs;
+            const double *b = b_val + pb * bs;
             for (int x = 0; x < nsf; ++x)
                 for (int z = 0; z < nsf; ++z) s += a[x * nsf + z] * b[z * nsf + x];
         }

@@ -1,0 +1,474 @@
+// The extern "C" surface of liblnv (declared in include/lnv.h).
+//
+// An LNV evaluation (Sec. 2, Eq. 3) runs, on the context stream:
+//   X = L S, Y = L H            push product, one kernel for both (shared A = L)
+//   T = S X, U = S Y            push product, one kernel for both (shared A = S)
+//   Z = L T  masked to R_X      pull product
+//   Tr[XY], Tr[ZY], Tr[XX], Tr[ZX] -> E, N_e   (one fused FP64 trace pass)
+//   Q = H Z  masked to R_L      pull product
+//   W = X^T U^T masked to R_L   pull product (= SL HLS = SLHLS)
+//   G = 6(U + U^T) - 4(Q^T + W + Q) on L's pattern
+// with R_X = R_L + R_SH and R_T = R_L + 2 R_SH: X, Y, T, U are the exact full
+// products (the minimum-image distance obeys the triangle inequality, so A B
+// vanishes beyond R_A + R_B), and Z is needed only inside R_X.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "lnv_impl.cuh"
+
+namespace lnv {
+
+static thread_local char g_err[512] = "";
+static std::atomic<int64_t> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+}  // namespace lnv
+
+using namespace lnv;
+
+struct lnv_system {
+    int nsf = 0;
+    lnv_prec prec = LNV_FP64;
+    int64_t n = 0;
+    int n_seg = 1;
+    double r_sh = 0, r_l = 0;
+    int64_t *seg_off_dev = nullptr;
+    lnv_pattern *P_sh = nullptr, *P_l = nullptr, *P_x = nullptr, *P_t = nullptr;
+    lnv_plan *pl_xy = nullptr, *pl_tu = nullptr, *pl_z = nullptr, *pl_q = nullptr, *pl_w = nullptr;
+    int64_t *sub_lt = nullptr;  // position in P_t of every block of P_l
+    void *own_ws = nullptr;
+    size_t own_ws_bytes = 0;
+    // stage timing (lnv_system_profile): events before XY, TU, Z, traces, Q, W, G and at the end
+    static constexpr int kStages = 7;
+    int profile = 0;
+    int profiled_grad = 0;
+    cudaEvent_t ev[kStages + 1] = {};
+};
+
+namespace {
+
+size_t elem_size(lnv_prec p) { return p == LNV_FP64 ? 8 : 4; }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct WsLayout {
+    size_t X, Y, Z, T, U, W, Q, rows, total;
+};
+
+WsLayout ws_layout(const lnv_system *s, int with_grad)
+{
+    WsLayout L{};
+    const size_t bs = (size_t)s->nsf * s->nsf * elem_size(s->prec);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    L.X = take(s->P_x->nnzb * bs);
+    L.Y = take(s->P_x->nnzb * bs);
+    L.Z = take(s->P_x->nnzb * bs);
+    L.T = take(s->P_t->nnzb * bs);
+    L.U = with_grad ? take(s->P_t->nnzb * bs) : 0;
+    L.W = with_grad ? take(s->P_l->nnzb * bs) : 0;
+    L.Q = with_grad ? take(s->P_l->nnzb * bs) : 0;
+    L.rows = take(sizeof(double) * 4 * (size_t)std::max<int64_t>(s->n, 1));
+    L.total = off;
+    return L;
+}
+
+void system_free(lnv_system *s)
+{
+    if (!s) return;
+    delete s->pl_xy; delete s->pl_tu; delete s->pl_z; delete s->pl_q; delete s->pl_w;
+    pattern_free(s->P_sh); pattern_free(s->P_l); pattern_free(s->P_x); pattern_free(s->P_t);
+    cudaFree(s->sub_lt);
+    cudaFree(s->seg_off_dev);
+    cudaFree(s->own_ws);
+    for (auto &e : s->ev)
+        if (e) cudaEventDestroy(e);
+    delete s;
+}
+
+lnv_status set_dev(const lnv_ctx *ctx)
+{
+    LNV_ARG(ctx, "null context");
+    LNV_CUDA(cudaSetDevice(ctx->device));
+    return LNV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lnv_last_error(void) { return g_err; }
+
+int64_t lnv_launch_count(void) { return g_launches.load(); }
+
+const char *lnv_version(void) { return "liblnv 0.1 (sm_103a)"; }
+
+lnv_status lnv_ctx_create(int device, void *cuda_stream, lnv_ctx **out)
+{
+    LNV_ARG(out, "null output");
+    int ndev = 0;
+    LNV_CUDA(cudaGetDeviceCount(&ndev));
+    LNV_ARG(device >= 0 && device < ndev, "device index out of range");
+    LNV_CUDA(cudaSetDevice(device));
+    lnv_ctx *c = new (std::nothrow) lnv_ctx();
+    if (!c) {
+        set_error("host allocation failed");
+        return LNV_ERR_OOM;
+    }
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    c->sm_count = v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    c->smem_optin = (size_t)v;
+    *out = c;
+    return LNV_OK;
+}
+
+lnv_status lnv_ctx_set_stream(lnv_ctx *ctx, void *cuda_stream)
+{
+    LNV_ARG(ctx, "null context");
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return LNV_OK;
+}
+
+lnv_status lnv_ctx_destroy(lnv_ctx *ctx)
+{
+    delete ctx;
+    return LNV_OK;
+}
+
+lnv_status lnv_pattern_build(lnv_ctx *ctx, const double *pos_dev, int64_t n_atoms,
+                             const double *cell_host, double cutoff, lnv_pattern **out)
+{
+    LNV_TRY(set_dev(ctx));
+    LNV_ARG(n_atoms >= 0 && n_atoms < INT32_MAX, "n_atoms out of range");
+    LNV_ARG(cell_host, "null cell");
+    int64_t off[2] = {0, n_atoms};
+    return pattern_build_impl(ctx, pos_dev, 1, off, cell_host, cutoff, out);
+}
+
+lnv_status lnv_pattern_build_batched(lnv_ctx *ctx, const double *pos_dev, int n_seg,
+                                     const int64_t *seg_off_host, const double *cells_host,
+                                     double cutoff, lnv_pattern **out)
+{
+    LNV_TRY(set_dev(ctx));
+    LNV_ARG(n_seg >= 1 && seg_off_host && cells_host, "bad segments");
+    LNV_ARG(seg_off_host[n_seg] < INT32_MAX, "too many atoms");
+    return pattern_build_impl(ctx, pos_dev, n_seg, seg_off_host, cells_host, cutoff, out);
+}
+
+lnv_status lnv_pattern_from_csr(lnv_ctx *ctx, int64_t n, const int64_t *row_ptr_dev,
+                                const int32_t *col_dev, lnv_pattern **out)
+{
+    LNV_TRY(set_dev(ctx));
+    LNV_ARG(out && row_ptr_dev && (n >= 0) && n < INT32_MAX, "bad pattern arguments");
+    lnv_pattern *p = new lnv_pattern();
+    p->n = n;
+    int64_t nnzb = 0;
+    cudaError_t e = cudaMemcpyAsync(&nnzb, row_ptr_dev + n, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && (nnzb < 0 || nnzb >= INT32_MAX)) {
+        pattern_free(p);
+        set_error("pattern block count %lld out of range", (long long)nnzb);
+        return LNV_ERR_PATTERN;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&p->row_ptr, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p->col, sizeof(int32_t) * std::max<int64_t>(nnzb, 1));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->row_ptr, row_ptr_dev, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess && nnzb > 0) {
+        LNV_ARG(col_dev, "null columns");
+        e = cudaMemcpyAsync(p->col, col_dev, sizeof(int32_t) * nnzb, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    if (e != cudaSuccess) {
+        pattern_free(p);
+        set_error("pattern copy failed: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? LNV_ERR_OOM : LNV_ERR_CUDA;
+    }
+    lnv_status s = pattern_validate(ctx, p);
+    if (s == LNV_OK) s = pattern_finish(ctx, p, false);
+    if (s != LNV_OK) {
+        pattern_free(p);
+        return s;
+    }
+    *out = p;
+    return LNV_OK;
+}
+
+lnv_status lnv_pattern_info(const lnv_pattern *p, int64_t *n, int64_t *nnzb,
+                            const int64_t **row_ptr_dev, const int32_t **col_dev,
+                            const int64_t **tr_dev, int *symmetric)
+{
+    LNV_ARG(p, "null pattern");
+    if (n) *n = p->n;
+    if (nnzb) *nnzb = p->nnzb;
+    if (row_ptr_dev) *row_ptr_dev = p->row_ptr;
+    if (col_dev) *col_dev = p->col;
+    if (tr_dev) *tr_dev = p->tr;
+    if (symmetric) *symmetric = p->symmetric;
+    return LNV_OK;
+}
+
+lnv_status lnv_pattern_destroy(lnv_pattern *p)
+{
+    pattern_free(p);
+    return LNV_OK;
+}
+
+lnv_status lnv_plan_product(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
+                            const lnv_pattern *C, int flags, lnv_plan **out)
+{
+    LNV_TRY(set_dev(ctx));
+    return plan_create(ctx, A, B, C, flags, out);
+}
+
+lnv_status lnv_plan_info(const lnv_plan *plan, int64_t *triples, int *mode)
+{
+    LNV_ARG(plan, "null plan");
+    if (triples) *triples = plan->triples;
+    if (mode) *mode = plan->mode;
+    return LNV_OK;
+}
+
+lnv_status lnv_plan_destroy(lnv_plan *plan)
+{
+    delete plan;
+    return LNV_OK;
+}
+
+lnv_status lnv_bsr_multiply(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec,
+                            const void *A_dev, const void *B_dev, void *C_dev)
+{
+    LNV_TRY(set_dev(ctx));
+    return multiply(ctx, plan, nsf, prec, A_dev, B_dev, C_dev);
+}
+
+lnv_status lnv_trace_product(lnv_ctx *ctx, const lnv_pattern *P, int nsf, lnv_prec prec,
+                             const void *A_dev, const void *B_dev, double *scratch_dev,
+                             double *out_dev)
+{
+    LNV_TRY(set_dev(ctx));
+    LNV_ARG(P && A_dev && B_dev && scratch_dev && out_dev, "null pointer");
+    const void *A[1] = {A_dev}, *B[1] = {B_dev};
+    LNV_TRY(trace_rows(ctx, P, nsf, prec, 1, A, B, scratch_dev));
+    return reduce_rows(ctx, scratch_dev, P->n, 1, 1, nullptr, out_dev, 1, 0);
+}
+
+lnv_status lnv_system_create(lnv_ctx *ctx, int nsf, lnv_prec prec, const double *pos_dev,
+                             int64_t n_atoms, int n_seg, const int64_t *seg_off_host,
+                             const double *cells_host, double r_sh, double r_l, lnv_system **out)
+{
+    LNV_TRY(set_dev(ctx));
+    LNV_ARG(out && pos_dev && cells_host, "null pointer");
+    LNV_ARG(nsf == 1 || nsf == 2 || nsf == 4 || nsf == 9, "NSF must be 1, 2, 4 or 9");
+    LNV_ARG(prec == LNV_FP64 || prec == LNV_FP32, "unknown precision");
+    LNV_ARG(n_seg >= 1, "n_seg < 1");
+    LNV_ARG(r_sh > 0 && r_l > 0, "ranges must be positive");
+    std::vector<int64_t> off(n_seg + 1);
+    if (n_seg == 1 && !seg_off_host) {
+        off[0] = 0;
+        off[1] = n_atoms;
+    } else {
+        LNV_ARG(seg_off_host, "seg_off_host is required for n_seg > 1");
+        for (int s = 0; s <= n_seg; ++s) off[s] = seg_off_host[s];
+        LNV_ARG(off[n_seg] == n_atoms, "segment offsets must end at n_atoms");
+    }
+    LNV_ARG(n_atoms >= 0 && n_atoms < INT32_MAX, "n_atoms out of range");
+    lnv_system *s = new lnv_system();
+    s->nsf = nsf;
+    s->prec = prec;
+    s->n = n_atoms;
+    s->n_seg = n_seg;
+    s->r_sh = r_sh;
+    s->r_l = r_l;
+    lnv_status st = LNV_OK;
+#define SYS_TRY(expr)              \
+    do {                           \
+        st = (expr);               \
+        if (st != LNV_OK) {        \
+            system_free(s);        \
+            return st;             \
+        }                          \
+    } while (0)
+    SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_sh, &s->P_sh));
+    SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_l, &s->P_l));
+    SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_l + r_sh, &s->P_x));
+    SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_l + 2 * r_sh, &s->P_t));
+    SYS_TRY(plan_create(ctx, s->P_l, s->P_sh, s->P_x, 0, &s->pl_xy));
+    SYS_TRY(plan_create(ctx, s->P_sh, s->P_x, s->P_t, 0, &s->pl_tu));
+    SYS_TRY(plan_create(ctx, s->P_l, s->P_t, s->P_x, 0, &s->pl_z));
+    SYS_TRY(plan_create(ctx, s->P_sh, s->P_x, s->P_l, 0, &s->pl_q));
+    SYS_TRY(plan_create(ctx, s->P_x, s->P_t, s->P_l, LNV_TRANS_A | LNV_TRANS_B, &s->pl_w));
+    cudaError_t e = cudaMalloc(&s->sub_lt, sizeof(int64_t) * std::max<int64_t>(s->P_l->nnzb, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&s->seg_off_dev, sizeof(int64_t) * (n_seg + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->seg_off_dev, off.data(), sizeof(int64_t) * (n_seg + 1), cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+        system_free(s);
+        set_error("system allocation failed: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? LNV_ERR_OOM : LNV_ERR_CUDA;
+    }
+    SYS_TRY(pattern_submap(ctx, s->P_l, s->P_t, s->sub_lt));
+#undef SYS_TRY
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        system_free(s);
+        set_error("system setup failed: %s", cudaGetErrorString(e));
+        return LNV_ERR_CUDA;
+    }
+    *out = s;
+    return LNV_OK;
+}
+
+lnv_status lnv_system_patterns(const lnv_system *sys, const lnv_pattern **sh, const lnv_pattern **l)
+{
+    LNV_ARG(sys, "null system");
+    if (sh) *sh = sys->P_sh;
+    if (l) *l = sys->P_l;
+    return LNV_OK;
+}
+
+lnv_status lnv_system_workspace_size(const lnv_system *sys, int with_grad, size_t *bytes)
+{
+    LNV_ARG(sys && bytes, "null pointer");
+    *bytes = ws_layout(sys, with_grad).total;
+    return LNV_OK;
+}
+
+lnv_status lnv_system_triples(const lnv_system *sys, int with_grad, int64_t *triples)
+{
+    LNV_ARG(sys && triples, "null pointer");
+    // X, Y (two products), T (and U), Z, then Q and W
+    int64_t t = 2 * sys->pl_xy->triples + sys->pl_tu->triples + sys->pl_z->triples;
+    if (with_grad) t += sys->pl_tu->triples + sys->pl_q->triples + sys->pl_w->triples;
+    *triples = t;
+    return LNV_OK;
+}
+
+lnv_status lnv_system_stage_triples(const lnv_system *sys, int64_t *t7)
+{
+    LNV_ARG(sys && t7, "null pointer");
+    t7[0] = 2 * sys->pl_xy->triples;  // X and Y
+    t7[1] = 2 * sys->pl_tu->triples;  // T and U (U only with the gradient)
+    t7[2] = sys->pl_z->triples;
+    t7[3] = 0;
+    t7[4] = sys->pl_q->triples;
+    t7[5] = sys->pl_w->triples;
+    t7[6] = 0;
+    return LNV_OK;
+}
+
+lnv_status lnv_system_destroy(lnv_system *sys)
+{
+    system_free(sys);
+    return LNV_OK;
+}
+
+lnv_status lnv_system_profile(lnv_system *sys, int enable)
+{
+    LNV_ARG(sys, "null system");
+    if (enable)
+        for (auto &e : sys->ev)
+            if (!e) LNV_CUDA(cudaEventCreate(&e));
+    sys->profile = enable ? 1 : 0;
+    return LNV_OK;
+}
+
+lnv_status lnv_system_stage_ms(lnv_system *sys, double *ms)
+{
+    LNV_ARG(sys && ms, "null pointer");
+    LNV_ARG(sys->ev[0], "profiling was never enabled");
+    const int last = sys->profiled_grad ? lnv_system::kStages : 4;
+    LNV_CUDA(cudaEventSynchronize(sys->ev[last]));
+    for (int k = 0; k < lnv_system::kStages; ++k) {
+        ms[k] = 0.0;
+        if (k < last) {
+            float f = 0.f;
+            LNV_CUDA(cudaEventElapsedTime(&f, sys->ev[k], sys->ev[k + 1]));
+            ms[k] = f;
+        }
+    }
+    return LNV_OK;
+}
+
+lnv_status lnv_energy_grad(lnv_ctx *ctx, lnv_system *sys, const void *S_dev, const void *H_dev,
+                           const void *L_dev, double *out_dev, void *G_dev, void *ws_dev,
+                           size_t ws_bytes)
+{
+    LNV_TRY(set_dev(ctx));
+    LNV_ARG(sys && S_dev && H_dev && L_dev && out_dev, "null pointer");
+    const int grad = G_dev != nullptr;
+    const WsLayout wl = ws_layout(sys, grad);
+    unsigned char *ws = (unsigned char *)ws_dev;
+    if (!ws) {
+        if (sys->own_ws_bytes < wl.total) {
+            cudaFree(sys->own_ws);
+            sys->own_ws = nullptr;
+            sys->own_ws_bytes = 0;
+            // the largest layout (with gradient) so later calls never reallocate
+            size_t need = ws_layout(sys, 1).total;
+            LNV_CUDA(cudaMalloc(&sys->own_ws, need));
+            sys->own_ws_bytes = need;
+        }
+        ws = (unsigned char *)sys->own_ws;
+    } else {
+        LNV_ARG(ws_bytes >= wl.total, "workspace smaller than lnv_system_workspace_size");
+    }
+    void *X = ws + wl.X, *Y = ws + wl.Y, *Z = ws + wl.Z, *T = ws + wl.T;
+    void *U = grad ? ws + wl.U : nullptr, *W = grad ? ws + wl.W : nullptr, *Q = grad ? ws + wl.Q : nullptr;
+    double *rows = (double *)(ws + wl.rows);
+    const int nsf = sys->nsf;
+    const lnv_prec pr = sys->prec;
+    auto mark = [&](int k) -> lnv_status {
+        if (sys->profile) LNV_CUDA(cudaEventRecord(sys->ev[k], ctx->stream));
+        return LNV_OK;
+    };
+    sys->profiled_grad = grad;
+    LNV_TRY(mark(0));
+    // a1: X = L S, Y = L H
+    LNV_TRY(multiply2(ctx, sys->pl_xy, nsf, pr, L_dev, S_dev, H_dev, X, Y));
+    LNV_TRY(mark(1));
+    // a2: T = S X (= SLS), U = S Y (= SLH)
+    if (grad) LNV_TRY(multiply2(ctx, sys->pl_tu, nsf, pr, S_dev, X, Y, T, U));
+    else LNV_TRY(multiply(ctx, sys->pl_tu, nsf, pr, S_dev, X, T));
+    LNV_TRY(mark(2));
+    // a3: Z = L T (= LSLS) on R_X
+    LNV_TRY(multiply(ctx, sys->pl_z, nsf, pr, L_dev, T, Z));
+    LNV_TRY(mark(3));
+    // a4: Tr[XY], Tr[ZY], Tr[XX], Tr[ZX] -> E, N_e per system
+    const void *ta[4] = {X, Z, X, Z}, *tb[4] = {Y, Y, X, X};
+    LNV_TRY(trace_rows(ctx, sys->P_x, nsf, pr, 4, ta, tb, rows));
+    LNV_TRY(reduce_rows(ctx, rows, sys->n, 4, sys->n_seg, sys->seg_off_dev, out_dev, 6, 2));
+    LNV_TRY(lnv_combine(ctx, sys->n_seg, out_dev));
+    LNV_TRY(mark(4));
+    if (grad) {
+        // a6: Q = H Z (= HLSLS) on R_L;  a5: W = X^T U^T (= SLHLS) on R_L
+        LNV_TRY(multiply(ctx, sys->pl_q, nsf, pr, H_dev, Z, Q));
+        LNV_TRY(mark(5));
+        LNV_TRY(multiply(ctx, sys->pl_w, nsf, pr, X, U, W));
+        LNV_TRY(mark(6));
+        // a7: G = 6(U + U^T) - 4(Q^T + W + Q) on L's pattern
+        LNV_TRY(grad_assemble(ctx, sys->P_l, sys->sub_lt, nsf, pr, U, W, Q, G_dev));
+        LNV_TRY(mark(7));
+    }
+    return LNV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// a1-a3, a5, a6: range-truncated block-sparse products C = mask_C(op(A) op(B)).
+//
+// The paper names sparse matrix multiplication as the main computational load
+// (Sec. 3) and K = 3LSL - 2LSLSL (Eq. 3) as the quantity built from it.  Each
+// product keeps only the blocks of C's range pattern.  Two kernels cover the
+// products of the LNV evaluation, chosen per plan from symbolic counts:
+//
+//  push  one CTA per output row i.  The row (in column chunks) is accumulated
+//        in shared memory: for each k of A's row i (serially), the threads
+//        spread over the blocks (k, j) of B's row k that fall in the chunk's
+//        column range, find j's slot by binary search in the staged column
+//        list and add A_ik B_kj.  Within one k every j is distinct, so no two
+//        threads touch one slot; a barrier separates successive k.  Sums are
+//        formed in k order (deterministic).  Best when B's rows fit C's row:
+//        X = LS, Y = LH, T = SX, U = SY (full-range products).
+//
+//  pull  one CTA per output row i, each thread owns OPT consecutive output
+//        blocks (i, j) and accumulates them in registers over k of A's row i
+//        (staged in shared memory in chunks).  For each k the thread finds
+//        its j's in B's sorted row k (binary search, then galloping), so the
+//        candidates tested are |A row| x |C row|.  Best when C's row is
+//        narrow: Z = L T masked to R_X, W = X^T U^T and Q = H Z masked to R_L.
+//
+// Operand transposes (op = ^T) read block (k, i) through the pattern's
+// transpose map and transpose it in registers.
+#include <algorithm>
+#include <cstring>
+
+#include "mult_kernels.cuh"
+
+namespace lnv {
+namespace {
+
+using prod::lower_bound_g;
+using prod::dispatch_trans;
+
+// ------------------------------------------------------------------ symbolic
+
+// Per row i: contributing triples, push scan length, pull candidates.
+template <bool TA, bool TB>
+__global__ void k_symbolic(int64_t n, const int64_t *__restrict__ a_rp,
+                           const int32_t *__restrict__ a_col, const int64_t *__restrict__ b_rp,
+                           const int32_t *__restrict__ b_col, const int64_t *__restrict__ c_rp,
+                           const int32_t *__restrict__ c_col, unsigned long long *counts)
+{
+    // one CTA per row; threads over C's row
+    const int64_t i = blockIdx.x;
+    if (i >= n) return;
+    const int64_t cb = c_rp[i], ce = c_rp[i + 1], ab = a_rp[i], ae = a_rp[i + 1];
+    unsigned long long trip = 0, scan = 0;
+    for (int64_t s = cb + threadIdx.x; s < ce; s += blockDim.x) {
+        int32_t j = c_col[s];
+        for (int64_t q = ab; q < ae; ++q) {
+            int32_t k = a_col[q];
+            int64_t bb = b_rp[k], be = b_rp[k + 1];
+            int64_t p = lower_bound_g(b_col, bb, be, j);
+            if (p < be && b_col[p] == j) ++trip;
+        }
+    }
+    if (threadIdx.x == 0)
+        for (int64_t q = ab; q < ae; ++q) scan += (unsigned long long)(b_rp[a_col[q] + 1] - b_rp[a_col[q]]);
+    atomicAdd(&counts[0], trip);
+    if (threadIdx.x == 0) {
+        atomicAdd(&counts[1], scan);
+        atomicAdd(&counts[2], (unsigned long long)((ae - ab) * (ce - cb)));
+    }
+}
+
+template <typename T>
+lnv_status dispatch_nsf(lnv_ctx *ctx, const lnv_plan *pl, int nsf, const void *A, const void *B1,
+                        const void *B2, void *C1, void *C2)
+{
+    switch (nsf) {
+    case 1: return dispatch_trans<T, 1>(ctx, pl, A, B1, B2, C1, C2);
+    case 2: return dispatch_trans<T, 2>(ctx, pl, A, B1, B2, C1, C2);
+    case 4: return dispatch_trans<T, 4>(ctx, pl, A, B1, B2, C1, C2);
+    case 9: return dispatch_trans<T, 9>(ctx, pl, A, B1, B2, C1, C2);
+    default:
+        set_error("NSF=%d is not built (1, 2, 4, 9 are)", nsf);
+        return LNV_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace
+
+lnv_status plan_create(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
+                       const lnv_pattern *C, int flags, lnv_plan **out)
+{
+    LNV_ARG(ctx && A && B && C && out, "null pointer");
+    LNV_ARG((flags & ~(LNV_TRANS_A | LNV_TRANS_B)) == 0, "unknown flags");
+    if (A->n != B->n || A->n != C->n) {
+        set_error("patterns of a product must have the same number of atoms (%lld, %lld, %lld)",
+                  (long long)A->n, (long long)B->n, (long long)C->n);
+        return LNV_ERR_PATTERN;
+    }
+    const int ta = (flags & LNV_TRANS_A) != 0, tb = (flags & LNV_TRANS_B) != 0;
+    if ((ta && !A->symmetric) || (tb && !B->symmetric)) {
+        set_error("a transposed operand needs a symmetric pattern");
+        return LNV_ERR_PATTERN;
+    }
+    lnv_plan *pl = new lnv_plan();
+    pl->A = A; pl->B = B; pl->C = C;
+    pl->trans_a = ta; pl->trans_b = tb;
+    pl->max_a_row = A->max_row;
+    pl->max_c_row = C->max_row;
+    unsigned long long *d_counts = nullptr;
+    unsigned long long h[3] = {0, 0, 0};
+    cudaError_t e = cudaMalloc(&d_counts, sizeof(h));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counts, 0, sizeof(h), ctx->stream);
+    if (e == cudaSuccess && C->n > 0) {
+        // Symmetric patterns: op(A)'s row pattern equals A's, op(B)'s equals B's.
+        k_symbolic<false, false><<<(unsigned)C->n, 128, 0, ctx->stream>>>(
+            C->n, A->row_ptr, A->col, B->row_ptr, B->col, C->row_ptr, C->col, d_counts);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_counts, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d_counts);
+    if (e != cudaSuccess) {
+        delete pl;
+        set_error("symbolic product pass failed: %s", cudaGetErrorString(e));
+        return LNV_ERR_CUDA;
+    }
+    pl->triples = (int64_t)h[0];
+    pl->push_scan = (int64_t)h[1];
+    pl->pull_cand = (int64_t)h[2];
+    pl->mode = pl->push_scan <= pl->pull_cand ? 0 : 1;
+    *out = pl;
+    return LNV_OK;
+}
+
+lnv_status multiply(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec, const void *A,
+                    const void *B, void *C)
+{
+    LNV_ARG(ctx && plan && A && B && C, "null pointer");
+    if (prec == LNV_FP64) return dispatch_nsf<double>(ctx, plan, nsf, A, B, nullptr, C, nullptr);
+    if (prec == LNV_FP32) return dispatch_nsf<float>(ctx, plan, nsf, A, B, nullptr, C, nullptr);
+    set_error("unknown precision %d", (int)prec);
+    return LNV_ERR_ARG;
+}
+
+lnv_status multiply2(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec, const void *A,
+                     const void *B1, const void *B2, void *C1, void *C2)
+{
+    LNV_ARG(ctx && plan && A && B1 && C1 && (B2 == nullptr) == (C2 == nullptr), "null pointer");
+    if (prec == LNV_FP64) return dispatch_nsf<double>(ctx, plan, nsf, A, B1, B2, C1, C2);
+    if (prec == LNV_FP32) return dispatch_nsf<float>(ctx, plan, nsf, A, B1, B2, C1, C2);
+    set_error("unknown precision %d", (int)prec);
+    return LNV_ERR_ARG;
+}
+
+}  // namespace lnv

@@ -1,0 +1,303 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: FP64 path, relative Frobenius error <= 1e-12 for matrices and
+relative error <= 1e-10 for E and N_e; FP32 path (FP32 products, FP64 traces
+and gradient combination), <= 2e-5 for both, measured against the oracle run
+on the FP64 inputs.  Integer work (patterns, transpose maps) is bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_0911_3584_gb300 import Context, LnvError, Pattern, Plan, System, trace_product
+from tests.gpu_util import oracle_lnv, rel_fro, rounded, to_dev, workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: (1e-12, 1e-10), torch.float32: (2e-5, 2e-5)}
+PREC = {torch.float64: "fp64", torch.float32: "fp32"}
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_device):
+    return Context(cuda_device)
+
+
+def _pattern_np(P):
+    return P.row_ptr.cpu().numpy(), P.col.cpu().numpy()
+
+
+# ------------------------------------------------------------------ a0 patterns
+
+@pytest.mark.parametrize("ncell,cutoffs", [(4, (2.5, 6.6, 8.0, 14.6, 21.2)), (2, (6.6, 21.2)),
+                                           (1, (3.0, 30.0))])
+def test_pattern_identical_to_oracle(ctx, ncell, cutoffs):
+    rng = np.random.default_rng(ncell)
+    pos, cell = synth.si_diamond_positions(ncell, rng)
+    for R in cutoffs:
+        P = Pattern.build(ctx, pos, cell, R)
+        rp, col = _pattern_np(P)
+        orp, ocol = oracle.pattern(pos, cell, R)
+        assert np.array_equal(rp, orp) and np.array_equal(col, ocol), R
+        assert P.symmetric
+        tr = P.tr.cpu().numpy()
+        rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+        assert np.array_equal(col[tr], rows) and np.array_equal(rows[tr], col)
+
+
+def test_pattern_random_orthorhombic_box_and_unwrapped_positions(ctx):
+    """Non-cubic box, positions partly outside [0, box): same set as the oracle."""
+    rng = np.random.default_rng(11)
+    cell = np.array([17.3, 23.9, 31.1])
+    pos = rng.uniform(-0.3, 1.3, size=(700, 3)) * cell
+    for R in (2.0, 5.5, 9.0, 12.0):
+        P = Pattern.build(ctx, pos, cell, R)
+        rp, col = _pattern_np(P)
+        orp, ocol = oracle.pattern(pos, cell, R)
+        assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+
+
+def test_pattern_isolated_atoms_and_single_atom(ctx):
+    pos = np.array([[0.0, 0.0, 0.0], [10.0, 10.0, 10.0], [20.0, 0.0, 5.0]])
+    P = Pattern.build(ctx, pos, [40.0, 40.0, 40.0], 3.0)
+    rp, col = _pattern_np(P)
+    assert rp.tolist() == [0, 1, 2, 3] and col.tolist() == [0, 1, 2]
+    P1 = Pattern.build(ctx, pos[:1], [5.0, 5.0, 5.0], 3.0)
+    assert _pattern_np(P1)[1].tolist() == [0]
+
+
+def test_pattern_batched_is_block_diagonal_union(ctx):
+    sizes = [2, 3, 1, 2]
+    pos_all, cells, off = [], [], [0]
+    for k, n in enumerate(sizes):
+        p, c = synth.si_diamond_positions(n, np.random.default_rng(100 + k))
+        pos_all.append(p)
+        cells.append(c)
+        off.append(off[-1] + p.shape[0])
+    P = Pattern.build_batched(ctx, np.concatenate(pos_all), off, cells, 8.0)
+    rp, col = _pattern_np(P)
+    exp_rp, exp_col = [0], []
+    for k in range(len(sizes)):
+        orp, ocol = oracle.pattern(pos_all[k], cells[k], 8.0)
+        exp_col.append(ocol + off[k])
+        exp_rp.extend((orp[1:] + exp_rp[-1]).tolist())
+    assert np.array_equal(rp, np.array(exp_rp)) and np.array_equal(col, np.concatenate(exp_col))
+
+
+def test_pattern_from_csr_rejects_unsorted_rows(ctx):
+    with pytest.raises(LnvError) as e:
+        Pattern.from_csr(ctx, [0, 2, 3], [1, 0, 1])
+    assert e.value.status == -4
+    P = Pattern.from_csr(ctx, [0, 2, 3], [0, 1, 1])
+    assert not P.symmetric
+
+
+# ------------------------------------------------------------------ a1-a3, a5, a6 products
+
+PRODUCT_CASES = [
+    # (ra, rb, rc, trans_a, trans_b): push- and pull-type patterns
+    (8.0, 6.6, 14.6, False, False),   # X = L S (full range)
+    (6.6, 14.6, 21.2, False, False),  # T = S X (full range)
+    (8.0, 21.2, 14.6, False, False),  # Z = L T masked
+    (14.6, 21.2, 8.0, True, True),    # W = X^T U^T masked
+    (6.6, 14.6, 8.0, False, False),   # Q = H Z masked
+    (8.0, 6.6, 14.6, True, False),    # transposed A, full range
+    (6.6, 8.0, 5.0, False, True),     # transposed B, masked
+]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("nsf", [1, 2, 4, 9])
+@pytest.mark.parametrize("case", PRODUCT_CASES)
+def test_masked_product_matches_oracle(ctx, dtype, nsf, case):
+    ra, rb, rc, ta, tb = case
+    rng = np.random.default_rng(nsf * 7 + int(ta) + 2 * int(tb))
+    ncell = 3 if nsf < 9 else 2
+    pos, cell = synth.si_diamond_positions(ncell, rng)
+    PA, PB, PC = (Pattern.build(ctx, pos, cell, r) for r in (ra, rb, rc))
+    oa, ob, oc = (oracle.pattern(pos, cell, r) for r in (ra, rb, rc))
+    A = oracle.csr(*oa, rng.standard_normal((oa[1].size, nsf, nsf)))
+    B = oracle.csr(*ob, rng.standard_normal((ob[1].size, nsf, nsf)))
+    A, B = rounded(A, dtype), rounded(B, dtype)
+    plan = Plan(ctx, PA, PB, PC, trans_a=ta, trans_b=tb)
+    C = plan.multiply(to_dev(A["val"], dtype, ctx.device), to_dev(B["val"], dtype, ctx.device))
+    ref = oracle.mprod(oracle.transpose(A) if ta else A, oracle.transpose(B) if tb else B, oc)
+    err = rel_fro(C.cpu().numpy(), ref["val"])
+    assert err <= TOL[dtype][0], (err, plan.mode)
+    assert plan.triples > 0
+
+
+def test_plan_modes_follow_symbolic_counts(ctx):
+    pos, cell = synth.si_diamond_positions(4, np.random.default_rng(0))
+    P = {r: Pattern.build(ctx, pos, cell, r) for r in (6.6, 8.0, 14.6, 21.2)}
+    assert Plan(ctx, P[8.0], P[6.6], P[14.6]).mode == "push"
+    assert Plan(ctx, P[6.6], P[14.6], P[21.2]).mode == "push"
+    assert Plan(ctx, P[8.0], P[21.2], P[14.6]).mode == "pull"
+    assert Plan(ctx, P[14.6], P[21.2], P[8.0], True, True).mode == "pull"
+
+
+def test_product_empty_and_ragged_rows(ctx):
+    """Isolated atoms (rows holding only the diagonal) next to a dense cluster."""
+    rng = np.random.default_rng(4)
+    cluster = rng.uniform(0, 6.0, size=(40, 3))
+    lone = np.array([[30.0, 30.0, 30.0], [45.0, 10.0, 20.0]])
+    pos = np.concatenate([cluster, lone])
+    cell = np.array([60.0, 60.0, 60.0])
+    for dtype in (torch.float64, torch.float32):
+        PA, PB, PC = (Pattern.build(ctx, pos, cell, r) for r in (3.0, 4.0, 5.0))
+        oa, ob, oc = (oracle.pattern(pos, cell, r) for r in (3.0, 4.0, 5.0))
+        A = rounded(oracle.csr(*oa, rng.standard_normal((oa[1].size, 4, 4))), dtype)
+        B = rounded(oracle.csr(*ob, rng.standard_normal((ob[1].size, 4, 4))), dtype)
+        C = Plan(ctx, PA, PB, PC).multiply(to_dev(A["val"], dtype, ctx.device),
+                                           to_dev(B["val"], dtype, ctx.device))
+        ref = oracle.mprod(A, B, oc)
+        assert rel_fro(C.cpu().numpy(), ref["val"]) <= TOL[dtype][0]
+
+
+# ------------------------------------------------------------------ a4 traces
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("nsf", [1, 4, 9])
+def test_trace_matches_oracle(ctx, dtype, nsf):
+    rng = np.random.default_rng(nsf)
+    pos, cell = synth.si_diamond_positions(2, rng)
+    P = Pattern.build(ctx, pos, cell, 7.0)
+    op = oracle.pattern(pos, cell, 7.0)
+    A = rounded(oracle.csr(*op, rng.standard_normal((op[1].size, nsf, nsf))), dtype)
+    B = rounded(oracle.csr(*op, rng.standard_normal((op[1].size, nsf, nsf))), dtype)
+    t = trace_product(ctx, P, to_dev(A["val"], dtype, ctx.device), to_dev(B["val"], dtype, ctx.device))
+    ref = oracle.trace(A, B)
+    assert abs(t.item() - ref) <= 1e-12 * np.sqrt(op[1].size) * nsf * nsf
+
+
+# ------------------------------------------------------------------ a1-a7 LNV evaluation
+
+def _gpu_lnv(ctx, w, dtype, grad=True, sysm=None):
+    if sysm is None:
+        sysm = System(ctx, w["nsf"], PREC[dtype], w["pos"], w["cell"], w["r_sh"], w["r_l"])
+    S, H, L = (to_dev(w[k], dtype, ctx.device) for k in ("S", "H", "L"))
+    out, G = sysm.energy_grad(S, H, L, grad=grad)
+    return sysm, out.cpu().numpy(), (G.cpu().numpy() if G is not None else None)
+
+
+def _check_lnv(out, G, ref, dtype):
+    tm, ts = TOL[dtype]
+    assert abs(out[0, 0] - ref["E"]) <= ts * abs(ref["E"]), (out[0, 0], ref["E"])
+    assert abs(out[0, 1] - ref["Ne"]) <= ts * abs(ref["Ne"]), (out[0, 1], ref["Ne"])
+    for k, t in enumerate(ref["traces"]):
+        assert abs(out[0, 2 + k] - t) <= ts * max(abs(t), 1e-3)
+    if G is not None:
+        assert rel_fro(G, ref["G"]) <= tm
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("ncell,nsf,r_sh,r_l", [(1, 1, 4.0, 5.0), (2, 2, 4.0, 5.0), (2, 4, 6.6, 8.0),
+                                                (2, 9, 3.0, 4.0), (3, 4, 3.0, 4.5), (3, 9, 4.0, 5.0)])
+def test_lnv_small_systems(ctx, dtype, ncell, nsf, r_sh, r_l):
+    w, S, H, L = workload(ncell, nsf, r_sh, r_l, seed=ncell * 10 + nsf)
+    sysm, out, G = _gpu_lnv(ctx, w, dtype)
+    assert np.array_equal(sysm.P_l.col.cpu().numpy(), w["l_col"])
+    ref = oracle_lnv(w, rounded(S, dtype), rounded(H, dtype), rounded(L, dtype))
+    _check_lnv(out, G, ref, dtype)
+
+
+@pytest.fixture(scope="module")
+def si512():
+    w, S, H, L = workload(4, 4, 6.6, 8.0, seed=0)
+    return w, oracle_lnv(w, S, H, L)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_lnv_512_atoms(ctx, si512, dtype):
+    """4x4x4 cells, NSF=4, R_L = 8 A (FP32 measured against the FP64 oracle)."""
+    w, ref = si512
+    _, out, G = _gpu_lnv(ctx, w, dtype)
+    _check_lnv(out, G, ref, dtype)
+
+
+@pytest.fixture(scope="module")
+def si4096():
+    w, S, H, L = workload(8, 4, 6.6, 8.0, seed=0)
+    return w, oracle_lnv(w, S, H, L)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_lnv_4096_atoms_full(ctx, si4096, dtype):
+    """The benchmark workload (8x8x8 cells, 4096 atoms, NSF=4, R_L = 8 A) in the
+    launch configuration the benchmark times, every output against the oracle."""
+    w, ref = si4096
+    _, out, G = _gpu_lnv(ctx, w, dtype)
+    _check_lnv(out, G, ref, dtype)
+
+
+def test_energy_only_matches_gradient_run(ctx):
+    w, S, H, L = workload(2, 4, 6.6, 8.0, seed=3)
+    sysm, out_g, _ = _gpu_lnv(ctx, w, torch.float64, grad=True)
+    _, out_e, G = _gpu_lnv(ctx, w, torch.float64, grad=False, sysm=sysm)
+    assert G is None
+    assert np.array_equal(out_g, out_e)
+
+
+def test_single_atom_closed_form(ctx):
+    """NSF = 1, one atom: E = 2h(3 l^2 s - 2 l^3 s^2), dE/dl = 2h(6 l s - 6 l^2 s^2)."""
+    s, h, l = 1.3, -0.7, 0.45
+    sysm = System(ctx, 1, "fp64", np.zeros((1, 3)), [10.0, 10.0, 10.0], 3.0, 3.0)
+    S, H, L = (torch.tensor([[[v]]], dtype=torch.float64, device=ctx.device) for v in (s, h, l))
+    out, G = sysm.energy_grad(S, H, L)
+    out = out.cpu().numpy()[0]
+    assert out[0] == pytest.approx(2 * h * (3 * l * l * s - 2 * l ** 3 * s * s), rel=1e-14)
+    assert out[1] == pytest.approx(2 * (3 * l * l * s * s - 2 * l ** 3 * s ** 3), rel=1e-14)
+    assert G.item() == pytest.approx(2 * h * (6 * l * s - 6 * l * l * s * s), rel=1e-14)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_deterministic_and_external_workspace(ctx, dtype):
+    w, S, H, L = workload(3, 4, 6.6, 8.0, seed=9)
+    sysm, out1, G1 = _gpu_lnv(ctx, w, dtype)
+    _, out2, G2 = _gpu_lnv(ctx, w, dtype, sysm=sysm)
+    assert np.array_equal(out1, out2) and np.array_equal(G1, G2)
+    ws = torch.empty(sysm.workspace_size(True), dtype=torch.uint8, device=ctx.device)
+    Sd, Hd, Ld = (to_dev(w[k], dtype, ctx.device) for k in ("S", "H", "L"))
+    out3, G3 = sysm.energy_grad(Sd, Hd, Ld, workspace=ws)
+    assert np.array_equal(out3.cpu().numpy(), out1) and np.array_equal(G3.cpu().numpy(), G1)
+
+
+# ------------------------------------------------------------------ a8 batched systems
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_systems_equal_single_runs(ctx, dtype):
+    sizes = [2, 3, 2, 4]
+    ws = [workload(n, 4, 6.6, 8.0, seed=1000 + k)[0] for k, n in enumerate(sizes)]
+    off = [0]
+    for w in ws:
+        off.append(off[-1] + w["pos"].shape[0])
+    sysb = System(ctx, 4, PREC[dtype], np.concatenate([w["pos"] for w in ws]), [w["cell"] for w in ws],
+                  6.6, 8.0, seg_off=off)
+    cat = {k: to_dev(np.concatenate([w[k] for w in ws]), dtype, ctx.device) for k in ("S", "H", "L")}
+    out_b, G_b = sysb.energy_grad(cat["S"], cat["H"], cat["L"])
+    out_b, G_b = out_b.cpu().numpy(), G_b.cpu().numpy()
+    gofs = 0
+    for k, w in enumerate(ws):
+        _, out, G = _gpu_lnv(ctx, w, dtype)
+        assert np.array_equal(out_b[k], out[0])
+        assert np.array_equal(G_b[gofs:gofs + G.shape[0]], G)
+        gofs += G.shape[0]
+
+
+def test_argument_errors(ctx):
+    w, S, H, L = workload(1, 4, 4.0, 5.0)
+    sysm = System(ctx, 4, "fp64", w["pos"], w["cell"], 4.0, 5.0)
+    S32 = to_dev(w["S"], torch.float32, ctx.device)
+    Sd, Hd, Ld = (to_dev(w[k], torch.float64, ctx.device) for k in ("S", "H", "L"))
+    with pytest.raises(ValueError):
+        sysm.energy_grad(S32, Hd, Ld)
+    with pytest.raises(ValueError):
+        sysm.energy_grad(Sd[:-1], Hd, Ld)
+    with pytest.raises(LnvError) as e:
+        System(ctx, 3, "fp64", w["pos"], w["cell"], 4.0, 5.0)
+    assert e.value.status == -1
+    ws = torch.empty(16, dtype=torch.uint8, device=ctx.device)
+    with pytest.raises(LnvError):
+        sysm.energy_grad(Sd, Hd, Ld, workspace=ws)

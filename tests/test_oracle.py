@@ -306,3 +306,18 @@ def test_energy_per_atom_constant_under_tiling():
     assert big["Ne"] == pytest.approx(8 * small["Ne"], rel=1e-12)
     Gs = tile(oracle.csr(L["rp"], L["col"], small["G"]), r_l)["val"]
     np.testing.assert_allclose(big["G"], Gs, rtol=0, atol=1e-12)
+
+
+def test_row_subset_products_and_traces_equal_full_ones():
+    """The row-restricted oracle entry points (used to time bounded samples)
+    give exactly the full result's rows."""
+    w, S, H, L = _si(3, 4, 6.6, 8.0, seed=2)
+    pat = oracle.pattern(w["pos"], w["cell"], 14.6)
+    full = oracle.mprod(L, S, pat)
+    rows = np.array([0, 5, 17, 100, 215])
+    part = oracle.mprod(L, S, pat, rows=rows)
+    for i in rows:
+        sl = slice(pat[0][i], pat[0][i + 1])
+        np.testing.assert_array_equal(part["val"][sl], full["val"][sl])
+    t_full, per_row = oracle.trace(full, full, row_part=True)
+    assert oracle.trace(full, full, rows=rows) == pytest.approx(per_row[rows].sum(), rel=1e-14)
