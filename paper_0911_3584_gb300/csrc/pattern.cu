@@ -445,7 +445,7 @@ lnv_status pattern_build_impl(lnv_ctx *ctx, const double *pos, int n_seg, const 
         k_bin_scatter<<<g, 256, 0, st>>>(atom_bin, n, bin_start, bin_count, bin_atoms);
         count_launch();
         STEP(cudaGetLastError());
-        k_neighbours<<<g, 128, 0, st>>>(pos, n, d_segs, atom_seg, atom_bin, bin_start, bin_atoms,
+        k_neighbours<<<g, 256, 0, st>>>(pos, n, d_segs, atom_seg, atom_bin, bin_start, bin_atoms,
                                          cutoff * cutoff, row_cnt, nullptr, nullptr);
         count_launch();
         STEP(cudaGetLastError());
@@ -461,7 +461,7 @@ lnv_status pattern_build_impl(lnv_ctx *ctx, const double *pos, int n_seg, const 
     }
     STEP(cudaMalloc(&p->col, sizeof(int32_t) * std::max<int64_t>(nnzb, 1)));
     if (n > 0) {
-        k_neighbours<<<g, 128, 0, st>>>(pos, n, d_segs, atom_seg, atom_bin, bin_start, bin_atoms,
+        k_neighbours<<<g, 256, 0, st>>>(pos, n, d_segs, atom_seg, atom_bin, bin_start, bin_atoms,
                                          cutoff * cutoff, nullptr, p->row_ptr, p->col);
         count_launch();
         STEP(cudaGetLastError());

@@ -96,7 +96,7 @@ class _DevView:
 
     def __init__(self, ptr: int, n: int, typestr: str):
         self.__cuda_array_interface__ = {
-            "shape": (n,), "typestr": typestr, "data": (ptr, True), "version": 3,
+            "shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3,
             "strides": None}
 
 
