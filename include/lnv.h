@@ -145,6 +145,22 @@ lnv_status lnv_trace_product(lnv_ctx *ctx, const lnv_pattern *P, int nsf, lnv_pr
                              const void *A_dev, const void *B_dev, double *scratch_dev,
                              double *out_dev);
 
+/* Tr[A B] like lnv_trace_product, for callers that cannot allocate device
+ * memory or pass scratch: for example code held to a fixed device-memory
+ * budget by its own pool, or an interface with no room for a scratch
+ * buffer.  The paper has no counterpart; this is a library convenience.
+ * The per-row partial sums live in a static device array of 262144 doubles
+ * (2 MiB) that every GPU loading the library keeps until exit; patterns with
+ * more rows fail with LNV_ERR_UNSUPPORTED.  The call allocates nothing.  Its
+ * first call on a device looks the array's address up (cudaGetSymbolAddress)
+ * and caches it: make that first call before any stream capture.  All calls
+ * on a device share the array, so calls whose kernels overlap on the GPU
+ * race; serialise them.  Every row's partial sum is written before it is
+ * read, so the array needs no clearing between calls. */
+lnv_status lnv_trace_product_noalloc(lnv_ctx *ctx, const lnv_pattern *P, int nsf,
+                                     lnv_prec prec, const void *A_dev, const void *B_dev,
+                                     double *out_dev);
+
 /* ---- a1-a7 fused: LNV energy, electron count and gradient -------------- */
 
 /* A system: positions, S and H on the range-r_sh pattern, L on the range-r_l

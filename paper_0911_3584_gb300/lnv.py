@@ -274,6 +274,24 @@ def trace_product(ctx: Context, P: Pattern, A_vals, B_vals, out=None, scratch=No
     return out
 
 
+def trace_product_noalloc(ctx: Context, P: Pattern, A_vals, B_vals, out=None) -> torch.Tensor:
+    """Tr[A B] through lnv_trace_product_noalloc: no device allocation inside
+    the library (its per-row sums use a built-in 2 MiB array, at most 262144
+    rows).  Calls on one device must not overlap on the GPU."""
+    nsf = A_vals.shape[-1]
+    prec = FP64 if A_vals.dtype == torch.float64 else FP32
+    a = _vals(A_vals, P, nsf, prec, "A")
+    b = _vals(B_vals, P, nsf, prec, "B")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=ctx.device)
+    f = lib().lnv_trace_product_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    _check(f(ctx.h, P.h, nsf, prec, a, b, _ptr(out)), "lnv_trace_product_noalloc")
+    return out
+
+
 class System:
     """One LNV system (or a batch of independent ones): patterns, plans, workspace."""
 
