@@ -126,8 +126,22 @@ lnv_status lnv_pattern_destroy(lnv_pattern *p);
 lnv_status lnv_plan_product(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
                             const lnv_pattern *C, int flags, lnv_plan **out);
 /* Symbolic counts of a plan: block triples (i, k, j) that contribute, and
- * the kernel chosen (0 push, 1 pull). */
+ * the kernel chosen: 0 push (shared-memory row accumulator), 1 pull with a
+ * binary search of B's row k per output, 2 pull walking B's row j
+ * (merge-join; needs a symmetric B pattern), 3 row groups of 4 atoms with a
+ * 16-bit position table of op(B), 4 row groups with per-column hit lists,
+ * 5 row groups with the table and a cp.async shared-memory pipeline (NSF = 4;
+ * other NSF run kernel 3), 6 row groups on tensor cores (mma.sync TF32 with
+ * a hi/lo split of both operands, FP32 accumulation; FP32 values, NSF = 4;
+ * other cases run kernel 3).
+ * The default is 3 when at least half of the table's candidates hit, else 4,
+ * when the tables fit a quarter of the free device memory. */
 lnv_status lnv_plan_info(const lnv_plan *plan, int64_t *triples, int *mode);
+/* Select the kernel of a plan (0..6 as above); all give the same result up
+ * to rounding order.  Kernels 3-5 build their tables on first selection
+ * (allocates, synchronises).  LNV_ERR_UNSUPPORTED if the kernel cannot run
+ * this plan. */
+lnv_status lnv_plan_set_kernel(lnv_ctx *ctx, lnv_plan *plan, int kernel);
 lnv_status lnv_plan_destroy(lnv_plan *plan);
 
 /* Numeric product on the context stream.  A_dev, B_dev, C_dev are value
@@ -184,6 +198,19 @@ lnv_status lnv_system_triples(const lnv_system *sys, int with_grad, int64_t *tri
  * counting both T and U). */
 lnv_status lnv_system_stage_triples(const lnv_system *sys, int64_t *t7);
 lnv_status lnv_system_destroy(lnv_system *sys);
+
+/* Kernel of each product stage (XY, TU, Z, -, Q, W, -; -1 for non-products),
+ * in the numbering of lnv_plan_info. */
+lnv_status lnv_system_stage_kernels(const lnv_system *sys, int *k7);
+
+/* Autotuner: runs one evaluation on S, H, L, then times every applicable
+ * kernel of each product stage (XY, TU, Z, Q, W) on those intermediates
+ * (reps launches each, CUDA events on the context stream) and keeps the
+ * fastest.  ms_out (5 x 7 values, may be NULL) receives the time of every
+ * (stage, kernel) pair tried, -1 for kernels that do not apply.  Allocates and synchronises; results do not change beyond rounding
+ * order.  Uses the system's own workspace. */
+lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev, const void *H_dev,
+                               const void *L_dev, int reps, double *ms_out);
 
 /* Stage timing: with enable != 0, lnv_energy_grad records CUDA events on the
  * context stream around its stages XY, TU, Z, traces, Q, W, G.

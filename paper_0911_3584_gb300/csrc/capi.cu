@@ -92,7 +92,7 @@ WsLayout ws_layout(const lnv_system *s, int with_grad)
 void system_free(lnv_system *s)
 {
     if (!s) return;
-    delete s->pl_xy; delete s->pl_tu; delete s->pl_z; delete s->pl_q; delete s->pl_w;
+    plan_free(s->pl_xy); plan_free(s->pl_tu); plan_free(s->pl_z); plan_free(s->pl_q); plan_free(s->pl_w);
     pattern_free(s->P_sh); pattern_free(s->P_l); pattern_free(s->P_x); pattern_free(s->P_t);
     cudaFree(s->sub_lt);
     cudaFree(s->seg_off_dev);
@@ -247,9 +247,15 @@ lnv_status lnv_plan_info(const lnv_plan *plan, int64_t *triples, int *mode)
     return LNV_OK;
 }
 
+lnv_status lnv_plan_set_kernel(lnv_ctx *ctx, lnv_plan *plan, int kernel)
+{
+    LNV_TRY(set_dev(ctx));
+    return plan_set_kernel(ctx, plan, kernel);
+}
+
 lnv_status lnv_plan_destroy(lnv_plan *plan)
 {
-    delete plan;
+    plan_free(plan);
     return LNV_OK;
 }
 
@@ -313,7 +319,9 @@ lnv_status lnv_system_create(lnv_ctx *ctx, int nsf, lnv_prec prec, const double 
     SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_l + 2 * r_sh, &s->P_t));
     SYS_TRY(plan_create(ctx, s->P_l, s->P_sh, s->P_x, 0, &s->pl_xy));
     SYS_TRY(plan_create(ctx, s->P_sh, s->P_x, s->P_t, 0, &s->pl_tu));
-    SYS_TRY(plan_create(ctx, s->P_l, s->P_t, s->P_x, 0, &s->pl_z));
+    // Z = L T: T = SLS is symmetric, so L T = L T^T; the transposed form lets
+    // the merge-join pull read T's row j in order instead of through tr.
+    SYS_TRY(plan_create(ctx, s->P_l, s->P_t, s->P_x, LNV_TRANS_B, &s->pl_z));
     SYS_TRY(plan_create(ctx, s->P_sh, s->P_x, s->P_l, 0, &s->pl_q));
     SYS_TRY(plan_create(ctx, s->P_x, s->P_t, s->P_l, LNV_TRANS_A | LNV_TRANS_B, &s->pl_w));
     cudaError_t e = cudaMalloc(&s->sub_lt, sizeof(int64_t) * std::max<int64_t>(s->P_l->nnzb, 1));
@@ -360,6 +368,98 @@ lnv_status lnv_system_triples(const lnv_system *sys, int with_grad, int64_t *tri
     if (with_grad) t += sys->pl_tu->triples + sys->pl_q->triples + sys->pl_w->triples;
     *triples = t;
     return LNV_OK;
+}
+
+lnv_status lnv_system_stage_kernels(const lnv_system *sys, int *k7)
+{
+    LNV_ARG(sys && k7, "null pointer");
+    k7[0] = sys->pl_xy->mode;
+    k7[1] = sys->pl_tu->mode;
+    k7[2] = sys->pl_z->mode;
+    k7[3] = -1;
+    k7[4] = sys->pl_q->mode;
+    k7[5] = sys->pl_w->mode;
+    k7[6] = -1;
+    return LNV_OK;
+}
+
+lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev, const void *H_dev,
+                               const void *L_dev, int reps, double *ms_out)
+{
+    LNV_TRY(set_dev(ctx));
+    LNV_ARG(sys && S_dev && H_dev && L_dev, "null pointer");
+    if (reps < 1) reps = 1;
+    // one evaluation fills the intermediates the products read
+    const WsLayout wl = ws_layout(sys, 1);
+    void *G = nullptr;
+    double *out = nullptr;
+    LNV_CUDA(cudaMalloc(&G, (size_t)sys->P_l->nnzb * sys->nsf * sys->nsf * elem_size(sys->prec) + 16));
+    cudaError_t e = cudaMalloc(&out, sizeof(double) * 6 * (size_t)sys->n_seg);
+    if (e != cudaSuccess) {
+        cudaFree(G);
+        set_error("autotune allocation: %s", cudaGetErrorString(e));
+        return LNV_ERR_OOM;
+    }
+    lnv_status st = lnv_energy_grad(ctx, sys, S_dev, H_dev, L_dev, out, G, nullptr, 0);
+    unsigned char *ws = (unsigned char *)sys->own_ws;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == LNV_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        set_error("autotune: event creation failed");
+        st = LNV_ERR_CUDA;
+    }
+    struct Stage {
+        lnv_plan *pl;
+        const void *A, *B1, *B2;
+        void *C1, *C2;
+    };
+    void *X = ws + wl.X, *Y = ws + wl.Y, *Z = ws + wl.Z, *T = ws + wl.T, *U = ws + wl.U;
+    void *W = ws + wl.W, *Q = ws + wl.Q;
+    Stage stages[5] = {{sys->pl_xy, L_dev, S_dev, H_dev, X, Y},
+                       {sys->pl_tu, S_dev, X, Y, T, U},
+                       {sys->pl_z, L_dev, T, nullptr, Z, nullptr},
+                       {sys->pl_q, H_dev, Z, nullptr, Q, nullptr},
+                       {sys->pl_w, X, U, nullptr, W, nullptr}};
+    for (int si = 0; si < 5 && st == LNV_OK; ++si) {
+        Stage &sg = stages[si];
+        const int orig = sg.pl->mode;
+        int best = orig;
+        float best_ms = 1e30f;
+        for (int k = 0; k < 7; ++k)
+            if (ms_out) ms_out[si * 7 + k] = -1.0;
+        for (int k : {0, 2, 3, 4, 5, 6}) {
+            if (k == 5 && sys->nsf != 4) continue;
+            // tensor-core kernel: FP32 values, NSF = 4 (3xTF32, FP32-level accuracy)
+            if (k == 6 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
+            if (plan_set_kernel(ctx, sg.pl, k) != LNV_OK) continue;
+            lnv_status rs = multiply2(ctx, sg.pl, sys->nsf, sys->prec, sg.A, sg.B1, sg.B2, sg.C1, sg.C2);
+            if (rs == LNV_OK && cudaEventRecord(e0, ctx->stream) == cudaSuccess) {
+                for (int r = 0; r < reps && rs == LNV_OK; ++r)
+                    rs = multiply2(ctx, sg.pl, sys->nsf, sys->prec, sg.A, sg.B1, sg.B2, sg.C1, sg.C2);
+                float ms = 0.f;
+                if (rs == LNV_OK && cudaEventRecord(e1, ctx->stream) == cudaSuccess &&
+                    cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+                    ms /= reps;
+                    if (ms_out) ms_out[si * 7 + k] = ms;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = k;
+                    }
+                }
+            }
+            if (rs != LNV_OK) {
+                st = rs;
+                break;
+            }
+        }
+        if (st == LNV_OK) st = plan_set_kernel(ctx, sg.pl, best);
+        else plan_set_kernel(ctx, sg.pl, orig);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(G);
+    cudaFree(out);
+    return st;
 }
 
 lnv_status lnv_system_stage_triples(const lnv_system *sys, int64_t *t7)

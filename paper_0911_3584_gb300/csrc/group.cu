@@ -1,0 +1,273 @@
+// Symbolic phase of the row-group product kernel.
+//
+// Each output row's products share nothing with the next row in a one-row
+// kernel, so every block op(B)_kj is fetched once per row that uses it.
+// Spatially close atoms have consecutive indices in a cell-ordered system, so
+// taking G consecutive rows together lets one fetch of op(B)_kj serve every
+// row of the group that holds A_ik.  This pass lists, per group, the k's and
+// j's the group touches and a 16-bit position table of op(B)_kj, so the
+// numeric kernel neither searches nor walks B's rows.  It runs once per plan.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <thread>
+#include <vector>
+
+#include "lnv_impl.cuh"
+
+namespace lnv {
+namespace {
+
+// bidx[k_local][j_local] of one group per CTA.
+__global__ void k_bidx(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
+                       const int64_t *__restrict__ j_off, const int32_t *__restrict__ j_list,
+                       const int64_t *__restrict__ bidx_off, const int64_t *__restrict__ b_rp,
+                       const int32_t *__restrict__ b_col, int trans_b, uint16_t *bidx)
+{
+    const int64_t g = blockIdx.x;
+    const int64_t kb = k_off[g], nk = k_off[g + 1] - kb;
+    const int64_t jb = j_off[g], nj = j_off[g + 1] - jb;
+    uint16_t *out = bidx + bidx_off[g];
+    const int64_t nj_pad = (nj + 7) & ~int64_t(7);  // rows padded to 16 bytes
+    for (int64_t t = threadIdx.x; t < nk * nj; t += blockDim.x) {
+        const int64_t kl = t / nj, jl = t - kl * nj;
+        const int32_t k = k_list[kb + kl], j = j_list[jb + jl];
+        // op(B)_kj: B^T -> block (j, k) in row j; B -> block (k, j) in row k
+        const int32_t row = trans_b ? j : k, key = trans_b ? k : j;
+        int64_t lo = b_rp[row], hi = b_rp[row + 1];
+        const int64_t r0 = lo;
+        while (lo < hi) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            if (b_col[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        const bool found = lo < b_rp[row + 1] && b_col[lo] == key;
+        out[kl * nj_pad + jl] = found ? (uint16_t)(lo - r0) : (uint16_t)0xFFFF;
+    }
+}
+
+// Hit lists: per (group, j) the k's of the group's K with op(B)_kj stored.
+// fill == nullptr: count into cnt[j_entry]; else write hk / hp at hoff.
+__global__ void k_hits(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
+                       const int64_t *__restrict__ j_off, const int32_t *__restrict__ j_list,
+                       const int64_t *__restrict__ b_rp, const int32_t *__restrict__ b_col,
+                       int trans_b, int64_t *cnt, const int64_t *__restrict__ hoff, uint16_t *hk,
+                       int32_t *hp)
+{
+    const int64_t g = blockIdx.x;
+    const int64_t kb = k_off[g], nk = k_off[g + 1] - kb;
+    const int64_t jb = j_off[g], nj = j_off[g + 1] - jb;
+    for (int64_t jl = threadIdx.x; jl < nj; jl += blockDim.x) {
+        const int32_t j = j_list[jb + jl];
+        int64_t c = 0, w = hp ? hoff[jb + jl] : 0;
+        for (int64_t kl = 0; kl < nk; ++kl) {
+            const int32_t k = k_list[kb + kl];
+            const int32_t row = trans_b ? j : k, key = trans_b ? k : j;
+            int64_t lo = b_rp[row], hi = b_rp[row + 1];
+            while (lo < hi) {
+                const int64_t mid = lo + ((hi - lo) >> 1);
+                if (b_col[mid] < key) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < b_rp[row + 1] && b_col[lo] == key) {
+                if (hp) {
+                    hk[w + c] = (uint16_t)kl;
+                    hp[w + c] = (int32_t)lo;
+                }
+                ++c;
+            }
+        }
+        if (!hp) cnt[jb + jl] = c;
+    }
+}
+
+template <typename X>
+lnv_status upload(const std::vector<X> &h, X **d, size_t *bytes)
+{
+    *d = nullptr;
+    if (h.empty()) return LNV_OK;
+    LNV_CUDA(cudaMalloc(d, sizeof(X) * h.size()));
+    LNV_CUDA(cudaMemcpy(*d, h.data(), sizeof(X) * h.size(), cudaMemcpyHostToDevice));
+    *bytes += sizeof(X) * h.size();
+    return LNV_OK;
+}
+
+}  // namespace
+
+lnv_status pattern_host_cols(lnv_ctx *ctx, const lnv_pattern *p)
+{
+    if ((int64_t)p->h_col.size() == p->nnzb) return LNV_OK;
+    p->h_col.resize(p->nnzb);
+    if (p->nnzb > 0) {
+        LNV_CUDA(cudaMemcpyAsync(p->h_col.data(), p->col, sizeof(int32_t) * p->nnzb,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        LNV_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return LNV_OK;
+}
+
+void group_plan_free(GroupPlan *gp)
+{
+    cudaFree(gp->k_off); cudaFree(gp->k_list); cudaFree(gp->apos);
+    cudaFree(gp->j_off); cudaFree(gp->j_list); cudaFree(gp->cpos);
+    cudaFree(gp->bidx_off); cudaFree(gp->bidx);
+    cudaFree(gp->hoff); cudaFree(gp->hk); cudaFree(gp->hp);
+    *gp = GroupPlan();
+}
+
+lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes, bool dense,
+                            bool sparse)
+{
+    const lnv_pattern *A = pl->A, *B = pl->B, *C = pl->C;
+    if (B->max_row >= 0xFFFF) {
+        set_error("row-group plan: B rows longer than 65534 blocks");
+        return LNV_ERR_UNSUPPORTED;
+    }
+    LNV_TRY(pattern_host_cols(ctx, A));
+    LNV_TRY(pattern_host_cols(ctx, C));
+    const int64_t n = C->n;
+    const int64_t ng = (n + G - 1) / G;
+    // sizes first (unions per group), in parallel over groups
+    std::vector<int64_t> nk(ng), nj(ng);
+    std::vector<std::vector<int32_t>> Ks(ng), Js(ng);
+    auto unite = [&](const lnv_pattern *P, int64_t r0, int64_t r1, std::vector<int32_t> &out) {
+        out.clear();
+        for (int64_t r = r0; r < r1; ++r)
+            out.insert(out.end(), P->h_col.begin() + P->h_row_ptr[r], P->h_col.begin() + P->h_row_ptr[r + 1]);
+        std::sort(out.begin(), out.end());
+        out.erase(std::unique(out.begin(), out.end()), out.end());
+    };
+    const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nth; ++t)
+            th.emplace_back([&, t] {
+                for (int64_t g = t; g < ng; g += nth) {
+                    const int64_t r0 = g * G, r1 = std::min(n, r0 + G);
+                    unite(A, r0, r1, Ks[g]);
+                    unite(C, r0, r1, Js[g]);
+                    nk[g] = (int64_t)Ks[g].size();
+                    nj[g] = (int64_t)Js[g].size();
+                }
+            });
+        for (auto &x : th) x.join();
+    }
+    std::vector<int64_t> k_off(ng + 1, 0), j_off(ng + 1, 0), b_off(ng + 1, 0);
+    int max_k = 0, max_j = 0;
+    for (int64_t g = 0; g < ng; ++g) {
+        k_off[g + 1] = k_off[g] + nk[g];
+        j_off[g + 1] = j_off[g] + nj[g];
+        b_off[g + 1] = b_off[g] + nk[g] * ((nj[g] + 7) & ~int64_t(7));
+        max_k = std::max<int>(max_k, (int)nk[g]);
+        max_j = std::max<int>(max_j, (int)nj[g]);
+    }
+    const size_t need = (dense ? sizeof(uint16_t) * (size_t)b_off[ng] : 0) +
+                        (sizeof(int32_t) * (1 + G)) * (size_t)(k_off[ng] + j_off[ng]);
+    if (need > budget_bytes) {
+        set_error("row-group plan needs %zu bytes, over the %zu budget", need, budget_bytes);
+        return LNV_ERR_UNSUPPORTED;
+    }
+    std::vector<int32_t> k_list(k_off[ng]), j_list(j_off[ng]);
+    std::vector<int32_t> apos((size_t)k_off[ng] * G, -1), cpos((size_t)j_off[ng] * G, -1);
+    {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nth; ++t)
+            th.emplace_back([&, t] {
+                for (int64_t g = t; g < ng; g += nth) {
+                    const int64_t r0 = g * G, r1 = std::min(n, r0 + G);
+                    std::copy(Ks[g].begin(), Ks[g].end(), k_list.begin() + k_off[g]);
+                    std::copy(Js[g].begin(), Js[g].end(), j_list.begin() + j_off[g]);
+                    for (int64_t r = r0; r < r1; ++r) {
+                        const int m = (int)(r - r0);
+                        for (int64_t q = A->h_row_ptr[r]; q < A->h_row_ptr[r + 1]; ++q) {
+                            const int64_t kl = std::lower_bound(Ks[g].begin(), Ks[g].end(), A->h_col[q]) - Ks[g].begin();
+                            apos[(size_t)(k_off[g] + kl) * G + m] = (int32_t)q;
+                        }
+                        for (int64_t q = C->h_row_ptr[r]; q < C->h_row_ptr[r + 1]; ++q) {
+                            const int64_t jl = std::lower_bound(Js[g].begin(), Js[g].end(), C->h_col[q]) - Js[g].begin();
+                            cpos[(size_t)(j_off[g] + jl) * G + m] = (int32_t)q;
+                        }
+                    }
+                    std::vector<int32_t>().swap(Ks[g]);
+                    std::vector<int32_t>().swap(Js[g]);
+                }
+            });
+        for (auto &x : th) x.join();
+    }
+    GroupPlan &gp = pl->grp;
+    gp.G = G;
+    gp.n_groups = ng;
+    gp.max_k = max_k;
+    gp.max_j = max_j;
+    size_t bytes = 0;
+    lnv_status s = LNV_OK;
+    if (s == LNV_OK) s = upload(k_off, &gp.k_off, &bytes);
+    if (s == LNV_OK) s = upload(k_list, &gp.k_list, &bytes);
+    if (s == LNV_OK) s = upload(apos, &gp.apos, &bytes);
+    if (s == LNV_OK) s = upload(j_off, &gp.j_off, &bytes);
+    if (s == LNV_OK) s = upload(j_list, &gp.j_list, &bytes);
+    if (s == LNV_OK) s = upload(cpos, &gp.cpos, &bytes);
+    if (s == LNV_OK) s = upload(b_off, &gp.bidx_off, &bytes);
+    gp.candidates = b_off[ng];
+    if (s == LNV_OK && dense && b_off[ng] > 0) {
+        cudaError_t e = cudaMalloc(&gp.bidx, sizeof(uint16_t) * (size_t)b_off[ng]);
+        if (e != cudaSuccess) {
+            set_error("row-group plan: %s", cudaGetErrorString(e));
+            s = e == cudaErrorMemoryAllocation ? LNV_ERR_OOM : LNV_ERR_CUDA;
+        } else {
+            bytes += sizeof(uint16_t) * (size_t)b_off[ng];
+            e = cudaMemsetAsync(gp.bidx, 0xFF, sizeof(uint16_t) * (size_t)b_off[ng], ctx->stream);
+            k_bidx<<<(unsigned)ng, 256, 0, ctx->stream>>>(gp.k_off, gp.k_list, gp.j_off, gp.j_list,
+                                                          gp.bidx_off, B->row_ptr, B->col, pl->trans_b, gp.bidx);
+            count_launch();
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) {
+                set_error("row-group position table: %s", cudaGetErrorString(e));
+                s = LNV_ERR_CUDA;
+            }
+        }
+    }
+    if (s == LNV_OK && sparse && j_off[ng] > 0) {
+        // count, scan, fill
+        int64_t *cnt = nullptr;
+        cudaError_t e = cudaMalloc(&cnt, sizeof(int64_t) * (size_t)j_off[ng]);
+        if (e == cudaSuccess) e = cudaMalloc(&gp.hoff, sizeof(int64_t) * (size_t)(j_off[ng] + 1));
+        if (e == cudaSuccess) {
+            k_hits<<<(unsigned)ng, 128, 0, ctx->stream>>>(gp.k_off, gp.k_list, gp.j_off, gp.j_list, B->row_ptr,
+                                                         B->col, pl->trans_b, cnt, nullptr, nullptr, nullptr);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            s = scan_exclusive(ctx->stream, cnt, j_off[ng], gp.hoff);
+            if (s == LNV_OK) {
+                e = cudaMemcpy(&gp.hits, gp.hoff + j_off[ng], sizeof(int64_t), cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess && gp.hits > 0) e = cudaMalloc(&gp.hk, sizeof(uint16_t) * (size_t)gp.hits);
+                if (e == cudaSuccess && gp.hits > 0) e = cudaMalloc(&gp.hp, sizeof(int32_t) * (size_t)gp.hits);
+                if (e == cudaSuccess && gp.hits > 0) {
+                    k_hits<<<(unsigned)ng, 128, 0, ctx->stream>>>(gp.k_off, gp.k_list, gp.j_off, gp.j_list,
+                                                                 B->row_ptr, B->col, pl->trans_b, nullptr,
+                                                                 gp.hoff, gp.hk, gp.hp);
+                    count_launch();
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+                bytes += sizeof(int64_t) * (size_t)(j_off[ng] + 1) + 6 * (size_t)gp.hits;
+            }
+        }
+        cudaFree(cnt);
+        if (s == LNV_OK && e != cudaSuccess) {
+            set_error("row-group hit lists: %s", cudaGetErrorString(e));
+            s = e == cudaErrorMemoryAllocation ? LNV_ERR_OOM : LNV_ERR_CUDA;
+        }
+    }
+    if (s != LNV_OK) {
+        group_plan_free(&gp);
+        return s;
+    }
+    gp.bytes = bytes;
+    return LNV_OK;
+}
+
+}  // namespace lnv

@@ -68,12 +68,47 @@ struct lnv_pattern {
     int symmetric = 0;
     int max_row = 0;             // longest row (host copy)
     std::vector<int64_t> h_row_ptr;  // host copy of row_ptr (for planning and tuning)
+    mutable std::vector<int32_t> h_col;  // host copy of col, filled on demand by the planner
+};
+
+// Row-group plan of a product (see group.cu): rows are taken G at a time; for
+// group g, K = sorted union of A's rows, J = sorted union of C's rows,
+// apos[k][m] / cpos[j][m] the positions of (row m, k) in A and (row m, j) in
+// C (-1 if absent), and bidx[k][j] the offset of op(B)_kj inside its B row
+// (B's row j when op(B) = B^T, row k otherwise; 0xFFFF if absent), rows of
+// the table padded to a multiple of 8 entries.
+struct GroupPlan {
+    int G = 0;
+    int64_t n_groups = 0;
+    int64_t *k_off = nullptr;    // [n_groups + 1]
+    int32_t *k_list = nullptr;   // [sum |K|]
+    int32_t *apos = nullptr;     // [sum |K|][G]
+    int64_t *j_off = nullptr;    // [n_groups + 1]
+    int32_t *j_list = nullptr;   // [sum |J|]
+    int32_t *cpos = nullptr;     // [sum |J|][G]
+    int64_t *bidx_off = nullptr; // [n_groups + 1]
+    uint16_t *bidx = nullptr;    // [sum |K| |J|]  (dense table; may be absent)
+    // sparse form: for each (group, j) the hits k (ascending) with op(B)_kj stored
+    int64_t *hoff = nullptr;     // [sum |J| + 1]
+    uint16_t *hk = nullptr;      // [hits] k position in the group's K list
+    int32_t *hp = nullptr;       // [hits] block index of op(B)_kj's stored block
+    int64_t hits = 0, candidates = 0;
+    int max_k = 0, max_j = 0;
+    size_t bytes = 0;
 };
 
 struct lnv_plan {
     const lnv_pattern *A, *B, *C;
     int trans_a, trans_b;
-    int mode;            // 0 push (row gather into a shared-memory row accumulator), 1 pull
+    // 0 push (row gather into a shared-memory row accumulator), 1 pull with a
+    // binary search per k, 2 pull with a merge-join walk (symmetric B pattern),
+    // 3 row groups with a dense position table, 4 row groups with hit lists
+    int mode;
+    GroupPlan grp;
+    // work items (row, first output slot) of the merge-join pull, for 64 and
+    // 128 outputs per CTA (device arrays)
+    int2 *items64 = nullptr, *items128 = nullptr;
+    int64_t n_items64 = 0, n_items128 = 0;
     int64_t triples;     // contributing block triples
     int64_t push_scan;   // B blocks a push kernel scans
     int64_t pull_cand;   // (k, j) candidates a pull kernel tests
@@ -95,6 +130,15 @@ lnv_status pattern_submap(lnv_ctx *ctx, const lnv_pattern *sub, const lnv_patter
 // Product internals (mult.cu)
 lnv_status plan_create(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
                        const lnv_pattern *C, int flags, lnv_plan **out);
+void plan_free(lnv_plan *plan);
+lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel);
+// Row-group plan (group.cu); returns LNV_ERR_UNSUPPORTED when the table would
+// not fit the budget or a B row is too long for 16-bit offsets.
+lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes, bool dense,
+                            bool sparse);
+lnv_status scan_exclusive(cudaStream_t st, const int64_t *in, int64_t n, int64_t *out);
+void group_plan_free(GroupPlan *gp);
+lnv_status pattern_host_cols(lnv_ctx *ctx, const lnv_pattern *p);
 lnv_status multiply(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec, const void *A,
                     const void *B, void *C);
 // Two products sharing A and the patterns of B and C: C1 = A B1, C2 = A B2.

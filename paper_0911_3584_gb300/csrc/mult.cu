@@ -25,6 +25,7 @@
 // transpose map and transpose it in registers.
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "mult_kernels.cuh"
 
@@ -83,6 +84,8 @@ lnv_status dispatch_nsf(lnv_ctx *ctx, const lnv_plan *pl, int nsf, const void *A
 
 }  // namespace
 
+lnv_status plan_pull_items(lnv_plan *pl);
+
 lnv_status plan_create(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
                        const lnv_pattern *C, int flags, lnv_plan **out)
 {
@@ -124,9 +127,95 @@ lnv_status plan_create(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
     pl->triples = (int64_t)h[0];
     pl->push_scan = (int64_t)h[1];
     pl->pull_cand = (int64_t)h[2];
-    pl->mode = pl->push_scan <= pl->pull_cand ? 0 : 1;
+    pl->mode = pl->push_scan <= pl->pull_cand ? 0 : (B->symmetric ? 2 : 1);
+    {
+        // Prefer the row-group kernel when its position table fits: a quarter of
+        // the free device memory, at most 16 GB.
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        const size_t budget = std::min<size_t>(free_b / 4, (size_t)16 << 30);
+        lnv_status gs = group_plan_build(ctx, pl, 4, budget, true, true);
+        // dense position table when most candidates hit, hit lists otherwise
+        if (gs == LNV_OK)
+            pl->mode = (pl->grp.candidates > 0 && 2 * pl->grp.hits >= pl->grp.candidates) ? 3 : 4;
+        else if (gs != LNV_ERR_UNSUPPORTED) {
+            plan_free(pl);
+            return gs;
+        }
+    }
+    if (pl->mode == 2) {
+        lnv_status is = plan_pull_items(pl);
+        if (is != LNV_OK) {
+            plan_free(pl);
+            return is;
+        }
+    }
     *out = pl;
     return LNV_OK;
+}
+
+// work items of the merge-join pull: (row, first slot) per 64 / 128 outputs
+lnv_status plan_pull_items(lnv_plan *pl)
+{
+    const lnv_pattern *C = pl->C;
+    if (pl->items64) return LNV_OK;
+    {
+        for (int chunk : {64, 128}) {
+            std::vector<int2> items;
+            for (int64_t r = 0; r < C->n; ++r) {
+                const int64_t nc = C->h_row_ptr[r + 1] - C->h_row_ptr[r];
+                for (int64_t s0 = 0; s0 < nc; s0 += chunk) items.push_back(make_int2((int)r, (int)s0));
+            }
+            int2 *d = nullptr;
+            if (!items.empty()) {
+                cudaError_t e2 = cudaMalloc(&d, sizeof(int2) * items.size());
+                if (e2 == cudaSuccess)
+                    e2 = cudaMemcpy(d, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+                if (e2 != cudaSuccess) {
+                    cudaFree(d);
+                    set_error("plan work items: %s", cudaGetErrorString(e2));
+                    return e2 == cudaErrorMemoryAllocation ? LNV_ERR_OOM : LNV_ERR_CUDA;
+                }
+            }
+            if (chunk == 64) {
+                pl->items64 = d;
+                pl->n_items64 = (int64_t)items.size();
+            } else {
+                pl->items128 = d;
+                pl->n_items128 = (int64_t)items.size();
+            }
+        }
+    }
+    return LNV_OK;
+}
+
+lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
+{
+    LNV_ARG(pl && kernel >= 0 && kernel <= 6, "kernel must be 0..6");
+    if (kernel == 2) {
+        if (!pl->B->symmetric) {
+            set_error("the merge-join pull needs a symmetric B pattern");
+            return LNV_ERR_UNSUPPORTED;
+        }
+        LNV_TRY(plan_pull_items(pl));
+    }
+    if (((kernel == 3 || kernel == 5 || kernel == 6) && !pl->grp.bidx) || (kernel == 4 && !pl->grp.hoff)) {
+        group_plan_free(&pl->grp);
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        LNV_TRY(group_plan_build(ctx, pl, 4, std::min<size_t>(free_b / 4, (size_t)16 << 30), true, true));
+    }
+    pl->mode = kernel;
+    return LNV_OK;
+}
+
+void plan_free(lnv_plan *plan)
+{
+    if (!plan) return;
+    cudaFree(plan->items64);
+    cudaFree(plan->items128);
+    group_plan_free(&plan->grp);
+    delete plan;
 }
 
 lnv_status multiply(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec, const void *A,

@@ -211,6 +211,928 @@ k_pull(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
     }
 }
 
+// ------------------------------------------------------------------ push2
+
+// Row-gather product with warp-owned column slices.  CTA = (row i, column
+// chunk [c0, c0 + chunk) of C's row), accumulated in shared memory.  Warp w
+// owns a contiguous slice of the chunk's slots.  For each k of A's row i (in
+// order), the blocks of B's row k whose column falls in warp w's slice form a
+// contiguous sub-range (B's rows are sorted); the CTA finds all sub-range
+// bounds with parallel binary searches once per staged k-chunk.  Lanes take
+// (block, output row x) tasks of the sub-range: within one k every column j
+// is distinct, so no two lanes touch one accumulator row, and a __syncwarp
+// separates successive k.  Each slot therefore sums its k's in order
+// (deterministic) and no CTA-wide barrier is needed inside the k loop.
+template <typename T, int NSF, int NOUT, bool TA, bool TB, int NW>
+__global__ void __launch_bounds__(NW * 32)
+k_push2(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
+        const int64_t *__restrict__ a_tr, const T *__restrict__ a_val,
+        const int64_t *__restrict__ b_rp, const int32_t *__restrict__ b_col,
+        const int64_t *__restrict__ b_tr, const T *__restrict__ b_val1,
+        const T *__restrict__ b_val2, const int64_t *__restrict__ c_rp,
+        const int32_t *__restrict__ c_col, T *__restrict__ c_val1, T *__restrict__ c_val2,
+        int chunk, int kchunk)
+{
+    constexpr int BS = NSF * NSF;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *acc = reinterpret_cast<T *>(smem_raw);                      // [NOUT][chunk][BS]
+    T *a_s = acc + (size_t)NOUT * chunk * BS;                      // [kchunk][BS]
+    int32_t *ccol = reinterpret_cast<int32_t *>(a_s + (size_t)kchunk * BS);  // [chunk]
+    int32_t *bnd = ccol + chunk;                                   // [kchunk][NW + 1]
+    int32_t *a_k = bnd + (size_t)kchunk * (NW + 1);                // [kchunk]
+
+    const int64_t i = blockIdx.x;
+    const int64_t cb = c_rp[i], ce = c_rp[i + 1];
+    const int64_t c0 = cb + (int64_t)blockIdx.y * chunk;
+    if (c0 >= ce) return;
+    const int cn = (int)min((int64_t)chunk, ce - c0);
+    const int64_t ab = a_rp[i], ae = a_rp[i + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // warp slices of the chunk: [sl0, sl1)
+    const int per_w = (cn + NW - 1) / NW;
+    const int sl0 = min(cn, warp * per_w), sl1 = min(cn, sl0 + per_w);
+
+    for (int t = threadIdx.x; t < cn; t += blockDim.x) ccol[t] = c_col[c0 + t];
+    for (int t = threadIdx.x; t < NOUT * chunk * BS; t += blockDim.x) acc[t] = T(0);
+
+    for (int64_t k0 = ab; k0 < ae; k0 += kchunk) {
+        const int kn = (int)min((int64_t)kchunk, ae - k0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < kn * BS; t += blockDim.x) {
+            const int qq = t / BS, e = t - qq * BS;
+            const int64_t q = k0 + qq;
+            if (TA) {
+                const int x = e / NSF, z = e % NSF;
+                a_s[t] = a_val[a_tr[q] * BS + z * NSF + x];
+            } else {
+                a_s[t] = a_val[q * BS + e];
+            }
+        }
+        for (int t = threadIdx.x; t < kn; t += blockDim.x) a_k[t] = a_col[k0 + t];
+        __syncthreads();
+        // sub-range bounds: bnd[qq][w] = first block of B's row k with column >=
+        // the first column of slice w (w = NW: past the chunk's last column)
+        for (int t = threadIdx.x; t < kn * (NW + 1); t += blockDim.x) {
+            const int qq = t / (NW + 1), w = t - qq * (NW + 1);
+            const int32_t k = a_k[qq];
+            const int s_w = min(cn, w * per_w);
+            const int32_t jkey = s_w < cn ? ccol[s_w] : ccol[cn - 1] + 1;
+            const int64_t rb = b_rp[k];
+            bnd[t] = (int32_t)(lower_bound_g(b_col, rb, b_rp[k + 1], jkey) - rb);
+        }
+        __syncthreads();
+        if (sl0 >= sl1) continue;
+        for (int qq = 0; qq < kn; ++qq) {
+            const int32_t k = a_k[qq];
+            const int64_t rb = b_rp[k];
+            const int64_t lo = rb + bnd[qq * (NW + 1) + warp], hi = rb + bnd[qq * (NW + 1) + warp + 1];
+            const int ntask = (int)(hi - lo) * NSF;
+            const T *as = a_s + (size_t)qq * BS;
+            for (int t = lane; t < ntask; t += 32) {
+                const int64_t p = lo + t / NSF;
+                const int x = t % NSF;
+                const int32_t j = __ldg(b_col + p);
+                // slot of j inside this warp's slice
+                int lo_s = sl0, hi_s = sl1;
+                while (lo_s < hi_s) {
+                    const int mid = (lo_s + hi_s) >> 1;
+                    if (ccol[mid] < j) lo_s = mid + 1;
+                    else hi_s = mid;
+                }
+                if (lo_s >= sl1 || ccol[lo_s] != j) continue;
+                const int64_t pb = TB ? b_tr[p] : p;
+                T ax[NSF];
+#pragma unroll
+                for (int z = 0; z < NSF; ++z) ax[z] = as[x * NSF + z];
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o) {
+                    const T *bblk = (o == 0 ? b_val1 : b_val2) + pb * BS;
+                    T *ar = acc + ((size_t)o * chunk + lo_s) * BS + x * NSF;
+                    T r[NSF];
+#pragma unroll
+                    for (int y = 0; y < NSF; ++y) r[y] = ar[y];
+#pragma unroll
+                    for (int z = 0; z < NSF; ++z) {
+                        T br[NSF];
+                        load_row<T, NSF, TB>(bblk, z, br);
+#pragma unroll
+                        for (int y = 0; y < NSF; ++y) r[y] = fma(ax[z], br[y], r[y]);
+                    }
+#pragma unroll
+                    for (int y = 0; y < NSF; ++y) ar[y] = r[y];
+                }
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NOUT * cn * BS; t += blockDim.x) {
+        const int o = t / (cn * BS), r = t - o * cn * BS;
+        T *dst = o == 0 ? c_val1 : c_val2;
+        dst[c0 * BS + r] = acc[(size_t)o * chunk * BS + r];
+    }
+}
+
+// ------------------------------------------------------------------ pull2 (merge-join)
+
+// Output-owner product for a symmetric B pattern.  Work item = (row i, first
+// output slot); the CTA's threads own outputs start+t, start+t+blockDim, ...
+// (OPT of them) and keep them in registers.  For output (i, j) the k's with
+// op(B)_kj stored are the columns of B's row j (the pattern is symmetric), so
+// each thread walks B's sorted row j forward, galloping to each k of A's row
+// i (sorted, staged in shared memory): no per-k search from the row start.
+// op(B)_kj is B[p]^T (TB: p is (j, k) in row j) or B[tr p] (block (k, j)).
+template <typename T, int NSF, int OPT, bool TA, bool TB>
+__global__ void __launch_bounds__(64)
+k_pull2(const int2 *__restrict__ items, const int64_t *__restrict__ a_rp,
+        const int32_t *__restrict__ a_col, const int64_t *__restrict__ a_tr,
+        const T *__restrict__ a_val, const int64_t *__restrict__ b_rp,
+        const int32_t *__restrict__ b_col, const int64_t *__restrict__ b_tr,
+        const T *__restrict__ b_val, const int64_t *__restrict__ c_rp,
+        const int32_t *__restrict__ c_col, T *__restrict__ c_val, int chunk_out, int kchunk)
+{
+    constexpr int BS = NSF * NSF;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *a_s = reinterpret_cast<T *>(smem_raw);                               // [kchunk][BS]
+    int32_t *a_k = reinterpret_cast<int32_t *>(a_s + (size_t)kchunk * BS);  // [kchunk]
+
+    const int2 it = items[blockIdx.x];
+    const int64_t i = it.x;
+    const int64_t cb = c_rp[i], ce = c_rp[i + 1];
+    const int64_t ab = a_rp[i], ae = a_rp[i + 1];
+    const int64_t s_end = min(ce, cb + (int64_t)it.y + chunk_out);
+    int64_t pos[OPT], end[OPT], cpos[OPT];
+    T acc[OPT][BS];
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+        cpos[o] = cb + it.y + threadIdx.x + (int64_t)o * blockDim.x;
+        pos[o] = end[o] = 0;
+        if (cpos[o] < s_end) {
+            const int32_t j = c_col[cpos[o]];
+            pos[o] = b_rp[j];
+            end[o] = b_rp[j + 1];
+        }
+#pragma unroll
+        for (int e = 0; e < BS; ++e) acc[o][e] = T(0);
+    }
+    for (int64_t k0 = ab; k0 < ae; k0 += kchunk) {
+        const int kn = (int)min((int64_t)kchunk, ae - k0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < kn * BS; t += blockDim.x) {
+            const int qq = t / BS, e = t - qq * BS;
+            const int64_t q = k0 + qq;
+            if (TA) {
+                const int x = e / NSF, z = e % NSF;
+                a_s[t] = a_val[a_tr[q] * BS + z * NSF + x];
+            } else {
+                a_s[t] = a_val[q * BS + e];
+            }
+        }
+        for (int t = threadIdx.x; t < kn; t += blockDim.x) a_k[t] = a_col[k0 + t];
+        __syncthreads();
+        for (int qq = 0; qq < kn; ++qq) {
+            const int32_t k = a_k[qq];
+            const T *as = a_s + (size_t)qq * BS;
+#pragma unroll
+            for (int o = 0; o < OPT; ++o) {
+                if (pos[o] >= end[o]) continue;
+                pos[o] = gallop_g(b_col, pos[o], end[o], k);
+                if (pos[o] >= end[o] || __ldg(b_col + pos[o]) != k) continue;
+                const T *bblk = b_val + (TB ? pos[o] : b_tr[pos[o]]) * BS;
+#pragma unroll
+                for (int z = 0; z < NSF; ++z) {
+                    T br[NSF];
+                    load_row<T, NSF, TB>(bblk, z, br);
+#pragma unroll
+                    for (int x = 0; x < NSF; ++x) {
+                        const T ax = as[x * NSF + z];
+#pragma unroll
+                        for (int y = 0; y < NSF; ++y) acc[o][x * NSF + y] = fma(ax, br[y], acc[o][x * NSF + y]);
+                    }
+                }
+                ++pos[o];
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+        if (cpos[o] >= s_end) continue;
+        T *dst = c_val + cpos[o] * BS;
+#pragma unroll
+        for (int e = 0; e < BS; ++e) dst[e] = acc[o][e];
+    }
+}
+
+// ------------------------------------------------------------------ row groups
+
+// Row-group product (plan built by group.cu).  CTA = (group g of G rows, a
+// chunk of the group's output columns J).  Lanes form groups of NSF, one per
+// output column j; lane r keeps column r of C_(m,j) for the G rows m (and
+// NOUT products sharing A) in registers.  For each k of the group's K (A's
+// blocks of the G rows staged in shared memory, zero where absent, with a
+// bitmask of the rows that hold A_mk), the lane reads the 16-bit position of
+// op(B)_kj (coalesced: the table is k-major), fetches its column r of
+// op(B)_kj once, and adds A_mk op(B)_kj for every row m in the mask.  Sums
+// run over k in ascending order (deterministic).  Outputs (m, j) outside C's
+// pattern are discarded at the store.
+// Vector helpers: NSF = 4 rows are 16 (FP32) or 32 (FP64) bytes, aligned in
+// every value array (blocks of 64 / 128 bytes from a 256-byte aligned base).
+template <typename T, int N>
+__device__ __forceinline__ void ld_row(const T *__restrict__ p, T (&v)[N], bool global)
+{
+    if constexpr (N == 4 && sizeof(T) == 4) {
+        const float4 q = global ? __ldg(reinterpret_cast<const float4 *>(p)) : *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if constexpr (N == 4 && sizeof(T) == 8) {
+        const double2 q0 = global ? __ldg(reinterpret_cast<const double2 *>(p)) : *reinterpret_cast<const double2 *>(p);
+        const double2 q1 = global ? __ldg(reinterpret_cast<const double2 *>(p) + 1) : *(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    } else if constexpr (N == 2 && sizeof(T) == 8) {
+        const double2 q = global ? __ldg(reinterpret_cast<const double2 *>(p)) : *reinterpret_cast<const double2 *>(p);
+        v[0] = q.x; v[1] = q.y;
+    } else if constexpr (N == 2 && sizeof(T) == 4) {
+        const float2 q = global ? __ldg(reinterpret_cast<const float2 *>(p)) : *reinterpret_cast<const float2 *>(p);
+        v[0] = q.x; v[1] = q.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = global ? __ldg(p + i) : p[i];
+    }
+}
+
+// The columns [c0, c0 + CW) of op(B)_kj held by one lane: bc[y][z] = op(B)[z][c0 + y].
+// op(B) = B^T: op(B)[z][c] = blk[c][z] -> rows c0.. of the stored block.
+// op(B) = B:   op(B)[z][c] = blk[z][c] -> a CW-wide slice of every row.
+template <typename T, int NSF, int CW, bool TB>
+__device__ __forceinline__ void ld_bcols(const T *__restrict__ blk, int c0, T (&bc)[CW][NSF])
+{
+    constexpr bool VEC = (NSF == 4) || (NSF == 2);
+    if constexpr (TB) {
+#pragma unroll
+        for (int y = 0; y < CW; ++y) {
+            if constexpr (VEC) ld_row<T, NSF>(blk + (c0 + y) * NSF, bc[y], true);
+            else {
+#pragma unroll
+                for (int z = 0; z < NSF; ++z) bc[y][z] = __ldg(blk + (c0 + y) * NSF + z);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int z = 0; z < NSF; ++z) {
+            T row[CW];
+            if constexpr (VEC && CW == NSF) ld_row<T, NSF>(blk + z * NSF, row, true);
+            else {
+#pragma unroll
+                for (int y = 0; y < CW; ++y) row[y] = __ldg(blk + z * NSF + c0 + y);
+            }
+#pragma unroll
+            for (int y = 0; y < CW; ++y) bc[y][z] = row[y];
+        }
+    }
+}
+
+// acc[x][y] += sum_z A[x][z] * bc[y][z] for the NSF rows x of one A block.
+template <typename T, int NSF, int CW, int NOUT>
+__device__ __forceinline__ void blk_fma(const T *am, const T (&bc)[NOUT][CW][NSF],
+                                        T (&acc)[NOUT][NSF][CW])
+{
+#pragma unroll
+    for (int x = 0; x < NSF; ++x) {
+        T a[NSF];
+        if constexpr (NSF == 4 || NSF == 2) ld_row<T, NSF>(am + x * NSF, a, false);
+        else {
+#pragma unroll
+            for (int z = 0; z < NSF; ++z) a[z] = am[x * NSF + z];
+        }
+#pragma unroll
+        for (int n = 0; n < NOUT; ++n)
+#pragma unroll
+            for (int y = 0; y < CW; ++y) {
+                T s = acc[n][x][y];
+#pragma unroll
+                for (int z = 0; z < NSF; ++z) s = fma(a[z], bc[n][y][z], s);
+                acc[n][x][y] = s;
+            }
+    }
+}
+
+// Staging helpers shared by the row-group kernels.
+// A's blocks of the G rows for k-chunk [k0, k0 + kn): one thread per (k, row)
+// block, loaded row by row (16-byte loads for NSF = 4) and stored transposed
+// when op(A) = A^T; zero where the row has no block.  msk[kk] gets the rows
+// holding A_(m, k).
+template <typename T, int NSF, int G, bool TA, typename S, bool MASK = true>
+__device__ __forceinline__ void stage_a(S *a_s, uint32_t *msk, const int32_t *__restrict__ apos,
+                                        const int64_t *__restrict__ a_tr, const T *__restrict__ a_val,
+                                        int64_t kbase, int kn)
+{
+    constexpr int BS = NSF * NSF;
+    for (int t = threadIdx.x; t < kn * G; t += blockDim.x) {
+        const int kk = t / G, m = t - kk * G;
+        const int32_t q = __ldg(apos + (kbase + kk) * G + m);
+        T blk[NSF][NSF];
+        if (q >= 0) {
+            const T *src = a_val + (TA ? __ldg(a_tr + q) : (int64_t)q) * BS;
+#pragma unroll
+            for (int x = 0; x < NSF; ++x) {
+                if constexpr (NSF == 4 || NSF == 2) ld_row<T, NSF>(src + x * NSF, blk[x], true);
+                else {
+#pragma unroll
+                    for (int z = 0; z < NSF; ++z) blk[x][z] = __ldg(src + x * NSF + z);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int x = 0; x < NSF; ++x)
+#pragma unroll
+                for (int z = 0; z < NSF; ++z) blk[x][z] = T(0);
+        }
+        S *dst = a_s + (size_t)t * BS;
+#pragma unroll
+        for (int x = 0; x < NSF; ++x)
+#pragma unroll
+            for (int z = 0; z < NSF; ++z) dst[x * NSF + z] = S(TA ? blk[z][x] : blk[x][z]);
+    }
+    if (MASK)
+        for (int kk = threadIdx.x; kk < kn; kk += blockDim.x) {
+            uint32_t mm = 0;
+#pragma unroll
+            for (int m = 0; m < G; ++m) mm |= (__ldg(apos + (kbase + kk) * G + m) >= 0 ? 1u : 0u) << m;
+            msk[kk] = mm;
+        }
+}
+
+// Position-table tile [kn][jc] of rows padded to a multiple of 8 entries,
+// loaded 16 bytes at a time; kflag[kk] = 1 when row kk has a hit.
+__device__ __forceinline__ void stage_ix(uint16_t *ixs, int32_t *kflag, const uint16_t *__restrict__ bx,
+                                         int64_t k0, int kn, int64_t nj_pad, int64_t j0, int jcn, int jc)
+{
+    for (int t = threadIdx.x; t < kn; t += blockDim.x) kflag[t] = 0;
+    __syncthreads();
+    const int vec = jc / 8;
+    for (int t = threadIdx.x; t < kn * vec; t += blockDim.x) {
+        const int kk = t / vec, v = t - kk * vec;
+        const int c = v * 8;
+        uint4 w = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        if (c < jcn) w = __ldg(reinterpret_cast<const uint4 *>(bx + (k0 + kk) * nj_pad + j0 + c));
+        uint16_t e[8];
+        memcpy(e, &w, 16);
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (c + u >= jcn) e[u] = 0xFFFF;
+            any |= e[u] != 0xFFFF;
+        }
+        memcpy(ixs + kk * jc + c, e, 16);
+        if (any) kflag[kk] = 1;
+    }
+}
+
+// List the flagged k's in order (warp 0, ballot prefix sums): kact[0..n), kact[cap] = n.
+__device__ __forceinline__ void compact_k(int32_t *kact, const int32_t *kflag, int kn, int cap)
+{
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    int base = 0;
+    for (int k0 = 0; k0 < kn; k0 += 32) {
+        const int kk = k0 + lane;
+        const bool f = kk < kn && kflag[kk];
+        const unsigned b = __ballot_sync(0xffffffffu, f);
+        if (f) kact[base + __popc(b & ((1u << lane) - 1u))] = kk;
+        base += __popc(b);
+    }
+    if (lane == 0) kact[cap] = base;
+}
+
+// Row-group product (plan built by group.cu).  CTA = (group g of G rows, a
+// chunk of the group's output columns J).  NSF / CW lanes share one output
+// column j; each keeps columns [c0, c0 + CW) of C_(m,j) for the G rows m (and
+// NOUT products sharing A) in registers, for OPT columns j per lane group.
+// For each k of the group's K, A's blocks of the G rows (staged in shared
+// memory, zero where absent, with a bitmask of the rows holding A_mk) are
+// applied to op(B)_kj, fetched once per lane:
+//   SPARSE = false: the 16-bit position of op(B)_kj comes from the dense
+//     table (a tile staged in shared memory per k-chunk); k's without a hit
+//     in the CTA's columns are skipped; the next k's blocks are fetched while
+//     the current ones are applied.
+//   SPARSE = true: each column walks its own hit list (ascending k), with the
+//     next hit's block fetched while the current one is applied.
+// Each A row is read once per k and applied to all OPT x NOUT outputs.  Sums
+// run over k in ascending order (deterministic).  Outputs (m, j) outside C's
+// pattern are discarded at the store.
+template <typename T, int NSF, int G, int NOUT, int CW, int OPT, bool TA, bool TB, bool SPARSE>
+__global__ void __launch_bounds__(128)
+k_grp(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
+      const int32_t *__restrict__ apos, const int64_t *__restrict__ j_off,
+      const int32_t *__restrict__ j_list, const int32_t *__restrict__ cpos,
+      const int64_t *__restrict__ bidx_off, const uint16_t *__restrict__ bidx,
+      const int64_t *__restrict__ hoff, const uint16_t *__restrict__ hk,
+      const int32_t *__restrict__ hp, const int64_t *__restrict__ a_tr,
+      const T *__restrict__ a_val, const int64_t *__restrict__ b_rp,
+      const T *__restrict__ b_val1, const T *__restrict__ b_val2, T *__restrict__ c_val1,
+      T *__restrict__ c_val2, int jc, int kchunk)
+{
+    static_assert(NOUT == 1 || NOUT == 2, "one or two products");
+    static_assert(NSF % CW == 0, "CW divides NSF");
+    constexpr int BS = NSF * NSF;
+    constexpr int LPJ = NSF / CW;    // lanes per output column
+    constexpr int JPW = 32 / LPJ;    // lane groups per warp
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *a_s = reinterpret_cast<T *>(smem_raw);                                    // [kchunk][G][BS]
+    int64_t *brow = reinterpret_cast<int64_t *>(a_s + (size_t)kchunk * G * BS);  // [kchunk]
+    uint32_t *msk = reinterpret_cast<uint32_t *>(brow + kchunk);                 // [kchunk]
+    int32_t *kact = reinterpret_cast<int32_t *>(msk + kchunk);                   // [kchunk + 2]
+    int32_t *kflag = kact + kchunk + 2;                                          // [kchunk]
+    uint16_t *ixs = reinterpret_cast<uint16_t *>(kflag + kchunk + 2);            // [kchunk][jc]
+
+    const int64_t g = blockIdx.x;
+    const int64_t kb = k_off[g], nk = k_off[g + 1] - kb;
+    const int64_t jb = j_off[g], nj = j_off[g + 1] - jb;
+    const int64_t nj_pad = (nj + 7) & ~int64_t(7);
+    const int64_t j0 = (int64_t)blockIdx.y * jc;
+    if (j0 >= nj) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int jg = lane / LPJ, c0 = (lane - jg * LPJ) * CW;
+    const int groups_cta = (blockDim.x >> 5) * JPW;
+    const int jcn = (int)min((int64_t)jc, nj - j0);
+    int col[OPT];
+    bool jv[OPT];
+    int64_t brj[OPT], ptr[OPT], pend[OPT];
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+        col[o] = warp * JPW + jg + o * groups_cta;
+        jv[o] = jg < JPW && col[o] < jcn;
+        brj[o] = (TB && jv[o]) ? b_rp[j_list[jb + j0 + col[o]]] : 0;
+        ptr[o] = (SPARSE && jv[o]) ? hoff[jb + j0 + col[o]] : 0;
+        pend[o] = (SPARSE && jv[o]) ? hoff[jb + j0 + col[o] + 1] : 0;
+    }
+    bool any_col = false;
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) any_col |= jv[o];
+
+    T acc[OPT][G][NOUT][NSF][CW];
+#pragma unroll
+    for (int o = 0; o < OPT; ++o)
+#pragma unroll
+        for (int m = 0; m < G; ++m)
+#pragma unroll
+            for (int n = 0; n < NOUT; ++n)
+#pragma unroll
+                for (int x = 0; x < NSF; ++x)
+#pragma unroll
+                    for (int y = 0; y < CW; ++y) acc[o][m][n][x][y] = T(0);
+
+    // apply A_mk (all active rows m) to the fetched blocks of the OPT columns
+    auto apply = [&](int kc, const T (&bc)[OPT][NOUT][CW][NSF], const bool (&h)[OPT], uint32_t mk) {
+        const T *ak = a_s + (size_t)kc * G * BS;
+#pragma unroll
+        for (int m = 0; m < G; ++m) {
+            if (!((mk >> m) & 1u)) continue;
+            const T *am = ak + m * BS;
+#pragma unroll
+            for (int x = 0; x < NSF; ++x) {
+                T a[NSF];
+                if constexpr (NSF == 4 || NSF == 2) ld_row<T, NSF>(am + x * NSF, a, false);
+                else {
+#pragma unroll
+                    for (int z = 0; z < NSF; ++z) a[z] = am[x * NSF + z];
+                }
+#pragma unroll
+                for (int o = 0; o < OPT; ++o) {
+                    if (!h[o]) continue;
+#pragma unroll
+                    for (int n = 0; n < NOUT; ++n)
+#pragma unroll
+                        for (int y = 0; y < CW; ++y) {
+                            T sacc = acc[o][m][n][x][y];
+#pragma unroll
+                            for (int z = 0; z < NSF; ++z) sacc = fma(a[z], bc[o][n][y][z], sacc);
+                            acc[o][m][n][x][y] = sacc;
+                        }
+                }
+            }
+        }
+    };
+    auto fetch_one = [&](int64_t p, T (&bc)[NOUT][CW][NSF]) {
+#pragma unroll
+        for (int n = 0; n < NOUT; ++n)
+            ld_bcols<T, NSF, CW, TB>((n == 0 ? b_val1 : b_val2) + p * BS, c0, bc[n]);
+    };
+    // dense: the blocks of active k number q (kact[q]) for every owned column
+    auto fetch_dense = [&](int kc, T (&bc)[OPT][NOUT][CW][NSF], bool (&h)[OPT]) {
+#pragma unroll
+        for (int o = 0; o < OPT; ++o) {
+            const uint16_t ix = jv[o] ? ixs[kc * jc + col[o]] : (uint16_t)0xFFFF;
+            h[o] = ix != 0xFFFF;
+            if (h[o]) fetch_one((TB ? brj[o] : brow[kc]) + ix, bc[o]);
+        }
+    };
+
+    for (int64_t k0 = 0; k0 < nk; k0 += kchunk) {
+        const int kn = (int)min((int64_t)kchunk, nk - k0);
+        __syncthreads();
+        stage_a<T, NSF, G, TA>(a_s, msk, apos, a_tr, a_val, kb + k0, kn);
+        if (!SPARSE) {
+            for (int t = threadIdx.x; t < kn; t += blockDim.x) brow[t] = TB ? 0 : b_rp[k_list[kb + k0 + t]];
+            stage_ix(ixs, kflag, bidx + bidx_off[g], k0, kn, nj_pad, j0, jcn, jc);
+            __syncthreads();
+            compact_k(kact, kflag, kn, kchunk);
+        }
+        __syncthreads();
+        if (!any_col) continue;
+        if (!SPARSE) {
+            const int na = kact[kchunk];
+            T bc0[OPT][NOUT][CW][NSF], bc1[OPT][NOUT][CW][NSF];
+            bool h0[OPT], h1[OPT];
+            // ping-pong over the active k's: the next k's blocks load during this k
+            if (na > 0) fetch_dense(kact[0], bc0, h0);
+            for (int q = 0; q < na; q += 2) {
+                const int ka = kact[q];
+                if (q + 1 < na) fetch_dense(kact[q + 1], bc1, h1);
+                apply(ka, bc0, h0, msk[ka]);
+                if (q + 1 >= na) break;
+                const int kb1 = kact[q + 1];
+                if (q + 2 < na) fetch_dense(kact[q + 2], bc0, h0);
+                apply(kb1, bc1, h1, msk[kb1]);
+            }
+        } else {
+            const int kend = (int)(k0 + kn);
+#pragma unroll
+            for (int o = 0; o < OPT; ++o) {
+                T bc0[OPT][NOUT][CW][NSF], bc1[OPT][NOUT][CW][NSF];
+                bool hh[OPT];
+#pragma unroll
+                for (int oo = 0; oo < OPT; ++oo) hh[oo] = oo == o;
+                int kl = ptr[o] < pend[o] ? (int)__ldg(hk + ptr[o]) : kend;
+                if (kl < kend) fetch_one(__ldg(hp + ptr[o]), bc0[o]);
+                while (kl < kend) {
+                    const int kc = kl - (int)k0;
+                    ++ptr[o];
+                    const int kl1 = ptr[o] < pend[o] ? (int)__ldg(hk + ptr[o]) : kend;
+                    if (kl1 < kend) fetch_one(__ldg(hp + ptr[o]), bc1[o]);
+                    apply(kc, bc0, hh, msk[kc]);
+                    kl = kl1;
+                    if (kl >= kend) break;
+                    const int kc1 = kl - (int)k0;
+                    ++ptr[o];
+                    const int kl2 = ptr[o] < pend[o] ? (int)__ldg(hk + ptr[o]) : kend;
+                    if (kl2 < kend) fetch_one(__ldg(hp + ptr[o]), bc0[o]);
+                    apply(kc1, bc1, hh, msk[kc1]);
+                    kl = kl2;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+        if (!jv[o]) continue;
+#pragma unroll
+        for (int m = 0; m < G; ++m) {
+            const int32_t pos = cpos[(jb + j0 + col[o]) * G + m];
+            if (pos < 0) continue;
+#pragma unroll
+            for (int n = 0; n < NOUT; ++n) {
+                T *dst = (n == 0 ? c_val1 : c_val2) + (int64_t)pos * BS;
+#pragma unroll
+                for (int x = 0; x < NSF; ++x)
+#pragma unroll
+                    for (int y = 0; y < CW; ++y) dst[x * NSF + c0 + y] = acc[o][m][n][x][y];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ row groups, pipelined
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Row-group product with a two-stage shared-memory pipeline (NSF = 4).  CTA =
+// (group g, JC = 64 output columns).  Per k-chunk of KC k's the CTA gathers
+// op(B)_kj for every (k, j) of the chunk x its columns into shared memory
+// with 16-byte cp.async copies (zero-filled where the dense position table
+// has no block), plus A's blocks of the G rows; while chunk c is multiplied
+// out of shared memory, chunk c+1's copies are in flight.  Four lanes share
+// an output column j (lane r keeps column r of C_(m,j) for every row m) and
+// each lane group owns two columns.  op(B) = B^T makes row r of the stored
+// block column r of op(B); otherwise the block is stored transposed in shared
+// memory so the same 16-byte read serves.  Sums run over k in ascending order.
+template <typename T, int G, int KC, bool TA, bool TB>
+__global__ void __launch_bounds__(128)
+k_gpipe(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
+        const int32_t *__restrict__ apos, const int64_t *__restrict__ j_off,
+        const int32_t *__restrict__ j_list, const int32_t *__restrict__ cpos,
+        const int64_t *__restrict__ bidx_off, const uint16_t *__restrict__ bidx,
+        const int64_t *__restrict__ a_tr, const T *__restrict__ a_val,
+        const int64_t *__restrict__ b_rp, const T *__restrict__ b_val, T *__restrict__ c_val)
+{
+    constexpr int NSF = 4, BS = 16, JC = 64, CPB = BS * sizeof(T) / 16;  // 16-byte chunks per block
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Bt = reinterpret_cast<T *>(smem_raw);                 // [2][KC][JC][BS]
+    T *At = Bt + 2 * KC * JC * BS;                           // [2][KC][G][BS]
+    uint32_t *msk = reinterpret_cast<uint32_t *>(At + 2 * KC * G * BS);  // [2][KC]
+
+    const int64_t g = blockIdx.x;
+    const int64_t kb = k_off[g], nk = k_off[g + 1] - kb;
+    const int64_t jb = j_off[g], nj = j_off[g + 1] - jb;
+    const int64_t j0 = (int64_t)blockIdx.y * JC;
+    if (j0 >= nj) return;
+    const int jcn = (int)min((int64_t)JC, nj - j0);
+    const uint16_t *bx = bidx + bidx_off[g];
+    const int tid = threadIdx.x;
+    const int lg = tid >> 2, r = tid & 3;  // lane group 0..31 owns columns lg and lg + 32
+    const int64_t nchunks = (nk + KC - 1) / KC;
+
+    // issue the copies of chunk c into buffer c & 1
+    auto issue = [&](int64_t c) {
+        const int buf = (int)(c & 1);
+        const int64_t k0 = c * KC;
+        const int kn = (int)min((int64_t)KC, nk - k0);
+        T *bt = Bt + buf * KC * JC * BS;
+        // op(B) blocks: KC x JC blocks of CPB 16-byte chunks
+        for (int t = tid; t < KC * JC * CPB; t += 128) {
+            const int blk = t / CPB, ch = t - blk * CPB;
+            const int kk = blk / JC, jj = blk - kk * JC;
+            const T *src = b_val;
+            int bytes = 0;
+            if (kk < kn && jj < jcn) {
+                const uint16_t ix = __ldg(bx + (k0 + kk) * ((nj + 7) & ~int64_t(7)) + j0 + jj);
+                if (ix != 0xFFFF) {
+                    const int64_t row = TB ? b_rp[j_list[jb + j0 + jj]] : b_rp[k_list[kb + k0 + kk]];
+                    src = b_val + (row + ix) * BS + ch * (16 / sizeof(T));
+                    bytes = 16;
+                }
+            }
+            if (TB) {
+                cp_async16(bt + (size_t)blk * BS + ch * (16 / sizeof(T)), src, bytes);
+            } else {
+                // stored block (k, j) row-major; op(B)[z][y] = blk[z][y].  Keep it as is:
+                // the consumer reads column r of op(B) from rows z (see below).
+                cp_async16(bt + (size_t)blk * BS + ch * (16 / sizeof(T)), src, bytes);
+            }
+        }
+        // A blocks of the G rows (transposed in registers when TA)
+        T *at = At + buf * KC * G * BS;
+        for (int t = tid; t < KC * G * BS; t += 128) {
+            const int kk = t / (G * BS), rem = t - kk * (G * BS), m = rem / BS, e = rem - m * BS;
+            T v = T(0);
+            if (kk < kn) {
+                const int32_t q = apos[(kb + k0 + kk) * G + m];
+                if (q >= 0) {
+                    if (TA) {
+                        const int x = e / NSF, z = e % NSF;
+                        v = a_val[a_tr[q] * BS + z * NSF + x];
+                    } else {
+                        v = a_val[(int64_t)q * BS + e];
+                    }
+                }
+            }
+            at[t] = v;
+        }
+        for (int t = tid; t < KC; t += 128) {
+            uint32_t mm = 0;
+            if (t < kn)
+#pragma unroll
+                for (int m = 0; m < G; ++m) mm |= (apos[(kb + k0 + t) * G + m] >= 0 ? 1u : 0u) << m;
+            msk[buf * KC + t] = mm;
+        }
+        cp_async_commit();
+    };
+
+    T acc[2][G][NSF];
+#pragma unroll
+    for (int o = 0; o < 2; ++o)
+#pragma unroll
+        for (int m = 0; m < G; ++m)
+#pragma unroll
+            for (int x = 0; x < NSF; ++x) acc[o][m][x] = T(0);
+
+    issue(0);
+    for (int64_t c = 0; c < nchunks; ++c) {
+        if (c + 1 < nchunks) {
+            issue(c + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int buf = (int)(c & 1);
+        const T *bt = Bt + buf * KC * JC * BS;
+        const T *at = At + buf * KC * G * BS;
+        const uint32_t *mk = msk + buf * KC;
+#pragma unroll 2
+        for (int kk = 0; kk < KC; ++kk) {
+            const uint32_t mm = mk[kk];
+            if (mm == 0) continue;  // past the end of K
+            T v[2][NSF];
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const T *blk = bt + (size_t)(kk * JC + lg + 32 * o) * BS;
+                // v[o][z] = op(B)_kj[z][r]
+                if (TB) ld_row<T, NSF>(blk + r * NSF, v[o], false);
+                else {
+#pragma unroll
+                    for (int z = 0; z < NSF; ++z) v[o][z] = blk[z * NSF + r];
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < G; ++m) {
+                if (!((mm >> m) & 1u)) continue;
+                const T *am = at + (kk * G + m) * BS;
+#pragma unroll
+                for (int x = 0; x < NSF; ++x) {
+                    T a[NSF];
+                    ld_row<T, NSF>(am + x * NSF, a, false);
+#pragma unroll
+                    for (int o = 0; o < 2; ++o) {
+                        T s = acc[o][m][x];
+#pragma unroll
+                        for (int z = 0; z < NSF; ++z) s = fma(a[z], v[o][z], s);
+                        acc[o][m][x] = s;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+        const int jj = lg + 32 * o;
+        if (jj >= jcn) continue;
+#pragma unroll
+        for (int m = 0; m < G; ++m) {
+            const int32_t pos = cpos[(jb + j0 + jj) * G + m];
+            if (pos < 0) continue;
+            T *dst = c_val + (int64_t)pos * BS;
+#pragma unroll
+            for (int x = 0; x < NSF; ++x) dst[x * NSF + r] = acc[o][m][x];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ row groups on tensor cores
+
+__device__ __forceinline__ uint32_t to_tf32(float f)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(f));
+    return r;
+}
+
+// D += A (16x4, row) * B (4x8, col), TF32 operands, FP32 accumulation.
+__device__ __forceinline__ void mma_tf32_k4(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k4.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+
+// Row-group product on tensor cores (FP32 values, NSF = 4, G = 4).  The G rows
+// of a group times NSF give M = 16, the tile of one mma.m16n8k4: rows (m, x),
+// columns (j, y) for two output columns j, reduction (k, z) over one k.  A's
+// blocks of the group are staged in shared memory already split into TF32
+// high and low parts (a = hi + lo); each op(B)_kj element is split in
+// registers, and hi*hi + hi*lo + lo*hi are accumulated in FP32 (the lo*lo
+// term is below FP32 rounding), which keeps FP32-level accuracy.  A warp owns
+// NT tiles (2 NT output columns); the position table gives op(B)_kj and a
+// warp skips a tile whose four lanes-groups all miss.  Sums run over k in
+// ascending order.
+template <int NOUT, int NT, bool TA, bool TB>
+__global__ void __launch_bounds__(128)
+k_gmma(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
+       const int32_t *__restrict__ apos, const int64_t *__restrict__ j_off,
+       const int32_t *__restrict__ j_list, const int32_t *__restrict__ cpos,
+       const int64_t *__restrict__ bidx_off, const uint16_t *__restrict__ bidx,
+       const int64_t *__restrict__ a_tr, const float *__restrict__ a_val,
+       const int64_t *__restrict__ b_rp, const float *__restrict__ b_val1,
+       const float *__restrict__ b_val2, float *__restrict__ c_val1, float *__restrict__ c_val2,
+       int kchunk)
+{
+    constexpr int G = 4, NSF = 4, BS = 16;
+    constexpr int JC = 4 * NT * 2;  // output columns per CTA
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *ahi = reinterpret_cast<uint32_t *>(smem_raw);   // [kchunk][G][BS] tf32 high
+    uint32_t *alo = ahi + (size_t)kchunk * G * BS;            // [kchunk][G][BS] tf32 low
+    int64_t *brow = reinterpret_cast<int64_t *>(alo + (size_t)kchunk * G * BS);  // [kchunk]
+    int32_t *kact = reinterpret_cast<int32_t *>(brow + kchunk);                  // [kchunk + 2]
+    int32_t *kflag = kact + kchunk + 2;                                          // [kchunk + 2]
+    uint16_t *ixs = reinterpret_cast<uint16_t *>(kflag + kchunk + 2);            // [kchunk][JC]
+
+    const int64_t g = blockIdx.x;
+    const int64_t kb = k_off[g], nk = k_off[g + 1] - kb;
+    const int64_t jb = j_off[g], nj = j_off[g + 1] - jb;
+    const int64_t nj_pad = (nj + 7) & ~int64_t(7);
+    const int64_t j0 = (int64_t)blockIdx.y * JC;
+    if (j0 >= nj) return;
+    const int jcn = (int)min((int64_t)JC, nj - j0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane >> 2, tig = lane & 3;  // mma groupID / thread-in-group
+    const int wbase = warp * NT * 2;            // first column of this warp
+    // the column this lane feeds into B fragments of tile nt: wbase + 2 nt + grp / 4
+    int64_t brj[NT];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const int c = wbase + 2 * nt + (grp >> 2);
+        brj[nt] = (TB && c < jcn) ? b_rp[j_list[jb + j0 + c]] : 0;
+    }
+    float acc[NOUT][NT][4];
+#pragma unroll
+    for (int n = 0; n < NOUT; ++n)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[n][nt][e] = 0.f;
+
+    const uint16_t *bx = bidx + bidx_off[g];
+    for (int64_t k0 = 0; k0 < nk; k0 += kchunk) {
+        const int kn = (int)min((int64_t)kchunk, nk - k0);
+        __syncthreads();
+        stage_a<float, NSF, G, TA, float, false>(reinterpret_cast<float *>(ahi), nullptr, apos, a_tr, a_val,
+                                                 kb + k0, kn);
+        __syncthreads();
+        // split A into TF32 high and low parts in place (ahi holds the FP32 values)
+        for (int t = threadIdx.x; t < kn * G * BS; t += blockDim.x) {
+            const float v = __uint_as_float(ahi[t]);
+            const uint32_t hi = to_tf32(v);
+            ahi[t] = hi;
+            alo[t] = to_tf32(v - __uint_as_float(hi));
+        }
+        for (int t = threadIdx.x; t < kn; t += blockDim.x) brow[t] = TB ? 0 : b_rp[k_list[kb + k0 + t]];
+        stage_ix(ixs, kflag, bx, k0, kn, nj_pad, j0, jcn, JC);
+        __syncthreads();
+        compact_k(kact, kflag, kn, kchunk);
+        __syncthreads();
+        const int na = kact[kchunk];
+        for (int q = 0; q < na; ++q) {
+            const int kk = kact[q];
+            // A fragment: rows (m, x) = grp and grp + 8, column z = tig
+            const uint32_t *ah = ahi + (size_t)kk * G * BS, *al = alo + (size_t)kk * G * BS;
+            const uint32_t ah0 = ah[grp * 4 + tig], ah1 = ah[32 + grp * 4 + tig];
+            const uint32_t al0 = al[grp * 4 + tig], al1 = al[32 + grp * 4 + tig];
+            const int64_t bk = brow[kk];
+            // B fragments of every tile first (independent loads), then the MMAs
+            float bv[NOUT][NT];
+            bool hit[NT];
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int c = wbase + 2 * nt + (grp >> 2);
+                const uint16_t ix = ixs[kk * JC + c];
+                hit[nt] = ix != 0xFFFF;
+                const int64_t p = (TB ? brj[nt] : bk) + (hit[nt] ? ix : 0);
+                // op(B)_kj[z = tig][y = grp % 4]
+                const int off = TB ? ((grp & 3) * NSF + tig) : (tig * NSF + (grp & 3));
+#pragma unroll
+                for (int n = 0; n < NOUT; ++n)
+                    bv[n][nt] = hit[nt] ? __ldg((n == 0 ? b_val1 : b_val2) + p * BS + off) : 0.f;
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                if (!__any_sync(0xffffffffu, hit[nt])) continue;
+#pragma unroll
+                for (int n = 0; n < NOUT; ++n) {
+                    const uint32_t bh = to_tf32(bv[n][nt]);
+                    const uint32_t bl = to_tf32(bv[n][nt] - __uint_as_float(bh));
+                    mma_tf32_k4(acc[n][nt], ah0, ah1, bh);
+                    mma_tf32_k4(acc[n][nt], ah0, ah1, bl);
+                    mma_tf32_k4(acc[n][nt], al0, al1, bh);
+                }
+            }
+        }
+    }
+    // D fragment: rows (m, x) = grp (c0, c1) and grp + 8 (c2, c3); columns
+    // (j, y) = 2 tig and 2 tig + 1 of the tile
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const int cc = 2 * tig;                     // column in the 8-wide tile
+        const int jj = wbase + 2 * nt + (cc >> 2);  // output column
+        const int y = cc & 3;
+        if (jj >= jcn) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int row = grp + 8 * h, m = row >> 2, x = row & 3;
+            const int32_t pos = cpos[(jb + j0 + jj) * G + m];
+            if (pos < 0) continue;
+#pragma unroll
+            for (int n = 0; n < NOUT; ++n) {
+                float *dst = (n == 0 ? c_val1 : c_val2) + (int64_t)pos * BS + x * NSF + y;
+                dst[0] = acc[n][nt][2 * h];
+                dst[1] = acc[n][nt][2 * h + 1];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ launch
 
 constexpr int kThreads = 128;
@@ -266,13 +1188,199 @@ lnv_status launch_pull(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const vo
     return LNV_OK;
 }
 
+constexpr int kGroupThreads = 128;
+
+
+
+template <int NSF>
+constexpr int group_cw()
+{
+    // lanes per output column: NSF / CW (NSF = 4: four lanes, one column each)
+    return NSF == 9 ? 3 : (NSF == 4 ? 1 : NSF);
+}
+
+template <typename T, int NSF, int G, int NOUT, bool TA, bool TB, bool SPARSE>
+lnv_status launch_grp(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
+                      const void *B2, void *C1, void *C2)
+{
+    constexpr int BS = NSF * NSF;
+    constexpr int CW = group_cw<NSF>();
+    constexpr int LPJ = NSF / CW;
+    constexpr int OPT = NSF == 4 ? 2 : 1;
+    const GroupPlan &gp = pl->grp;
+    if (gp.n_groups == 0 || gp.max_j == 0) return LNV_OK;
+    if (SPARSE ? !gp.hoff : !gp.bidx) {
+        set_error("row-group plan lacks the %s", SPARSE ? "hit lists" : "position table");
+        return LNV_ERR_UNSUPPORTED;
+    }
+    const int jc = (kGroupThreads / 32) * (32 / LPJ) * OPT;
+    const size_t per_k = (size_t)G * BS * sizeof(T) + sizeof(int64_t) + sizeof(uint32_t) +
+                         2 * sizeof(int32_t) + (SPARSE ? 0 : sizeof(uint16_t) * (size_t)jc);
+    int kchunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(gp.max_k, 1),
+                                                           (SPARSE ? 40 : 32) * 1024 / per_k));
+    const size_t smem = (size_t)kchunk * per_k + 128;
+    auto kern = k_grp<T, NSF, G, NOUT, CW, OPT, TA, TB, SPARSE>;
+    if (smem > 48 * 1024)
+        LNV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)gp.n_groups, (unsigned)((gp.max_j + jc - 1) / jc));
+    kern<<<grid, kGroupThreads, smem, ctx->stream>>>(
+        gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list, gp.cpos, gp.bidx_off, gp.bidx, gp.hoff,
+        gp.hk, gp.hp, pl->A->tr, (const T *)A, pl->B->row_ptr, (const T *)B1, (const T *)B2,
+        (T *)C1, (T *)C2, jc, kchunk);
+    LNV_LAUNCHED();
+    return LNV_OK;
+}
+
+template <typename T, bool TA, bool TB>
+lnv_status launch_gpipe(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B, void *C)
+{
+    constexpr int G = 4, BS = 16, JC = 64;
+    constexpr int KC = sizeof(T) == 4 ? 8 : 4;
+    const GroupPlan &gp = pl->grp;
+    if (gp.n_groups == 0 || gp.max_j == 0) return LNV_OK;
+    const size_t smem = sizeof(T) * (2 * KC * JC * BS + 2 * KC * G * BS) + sizeof(uint32_t) * 2 * KC + 64;
+    auto kern = k_gpipe<T, G, KC, TA, TB>;
+    LNV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)gp.n_groups, (unsigned)((gp.max_j + JC - 1) / JC));
+    kern<<<grid, 128, smem, ctx->stream>>>(gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list,
+                                          gp.cpos, gp.bidx_off, gp.bidx, pl->A->tr, (const T *)A,
+                                          pl->B->row_ptr, (const T *)B, (T *)C);
+    LNV_LAUNCHED();
+    return LNV_OK;
+}
+
+template <int NOUT, bool TA, bool TB>
+lnv_status launch_gmma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
+                       const void *B2, void *C1, void *C2)
+{
+    constexpr int G = 4, BS = 16, NT = 8, JC = 4 * NT * 2;
+    const GroupPlan &gp = pl->grp;
+    if (gp.n_groups == 0 || gp.max_j == 0) return LNV_OK;
+    if (!gp.bidx) {
+        set_error("row-group plan lacks the position table");
+        return LNV_ERR_UNSUPPORTED;
+    }
+    const size_t per_k = 2 * (size_t)G * BS * sizeof(uint32_t) + sizeof(int64_t) + 2 * sizeof(int32_t) +
+                         sizeof(uint16_t) * JC;
+    int kchunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(gp.max_k, 1), (32 * 1024) / per_k));
+    const size_t smem = (size_t)kchunk * per_k + 128;
+    auto kern = k_gmma<NOUT, NT, TA, TB>;
+    if (smem > 48 * 1024)
+        LNV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)gp.n_groups, (unsigned)((gp.max_j + JC - 1) / JC));
+    kern<<<grid, 128, smem, ctx->stream>>>(gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list, gp.cpos,
+                                          gp.bidx_off, gp.bidx, pl->A->tr, (const float *)A,
+                                          pl->B->row_ptr, (const float *)B1, (const float *)B2,
+                                          (float *)C1, (float *)C2, kchunk);
+    LNV_LAUNCHED();
+    return LNV_OK;
+}
+
+template <typename T, int NSF, int NOUT, bool TA, bool TB>
+lnv_status launch_group(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
+                        const void *B2, void *C1, void *C2)
+{
+    if constexpr (NSF == 4 && sizeof(T) == 4) {
+        if (pl->mode == 6) return launch_gmma<NOUT, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
+    }
+    if constexpr (NSF == 4) {
+        if (pl->mode == 5) {
+            LNV_TRY((launch_gpipe<T, TA, TB>(ctx, pl, A, B1, C1)));
+            if (B2) LNV_TRY((launch_gpipe<T, TA, TB>(ctx, pl, A, B2, C2)));
+            return LNV_OK;
+        }
+    }
+    if (pl->grp.G != 4) {
+        set_error("row-group size %d is not built (4 is)", pl->grp.G);
+        return LNV_ERR_UNSUPPORTED;
+    }
+    // Two fused products need two register accumulators per row; for FP64 and
+    // for NSF = 9 that exceeds the register file, so they run one at a time.
+    if constexpr (NOUT == 2 && (sizeof(T) == 8 || NSF > 4)) {
+        LNV_TRY((launch_group<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr)));
+        return launch_group<T, NSF, 1, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr);
+    } else {
+        if (pl->mode == 4) return launch_grp<T, NSF, 4, NOUT, TA, TB, true>(ctx, pl, A, B1, B2, C1, C2);
+        return launch_grp<T, NSF, 4, NOUT, TA, TB, false>(ctx, pl, A, B1, B2, C1, C2);
+    }
+}
+
+constexpr int kPush2Warps = 4;
+
+template <typename T, int NSF, int NOUT, bool TA, bool TB>
+lnv_status launch_push2(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
+                        const void *B2, void *C1, void *C2)
+{
+    constexpr int BS = NSF * NSF;
+    constexpr int NW = kPush2Warps;
+    const lnv_pattern *PA = pl->A, *PB = pl->B, *PC = pl->C;
+    if (PC->n == 0 || PC->max_row == 0) return LNV_OK;
+    // accumulator chunk: 32 KB of shared memory, a multiple of the warp count
+    int chunk = (int)((32 * 1024) / ((size_t)NOUT * BS * sizeof(T)));
+    chunk = std::max(NW, std::min(chunk, ((PC->max_row + NW - 1) / NW) * NW));
+    chunk = (chunk / NW) * NW;
+    int kchunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(PA->max_row, 1),
+                                                            (16 * 1024) / (BS * sizeof(T))));
+    size_t smem = (size_t)NOUT * chunk * BS * sizeof(T) + (size_t)kchunk * BS * sizeof(T) +
+                  sizeof(int32_t) * ((size_t)chunk + (size_t)kchunk * (NW + 1) + kchunk) + 16;
+    auto kern = k_push2<T, NSF, NOUT, TA, TB, NW>;
+    LNV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)PC->n, (unsigned)((PC->max_row + chunk - 1) / chunk));
+    kern<<<grid, NW * 32, smem, ctx->stream>>>(
+        PA->row_ptr, PA->col, PA->tr, (const T *)A, PB->row_ptr, PB->col, PB->tr, (const T *)B1,
+        (const T *)B2, PC->row_ptr, PC->col, (T *)C1, (T *)C2, chunk, kchunk);
+    LNV_LAUNCHED();
+    return LNV_OK;
+}
+
+constexpr int kPull2Threads = 64;
+
+template <typename T, int NSF>
+constexpr int pull2_opt()
+{
+    return NSF >= 9 ? 1 : 2;
+}
+
+template <typename T, int NSF, bool TA, bool TB>
+lnv_status launch_pull2(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B, void *C)
+{
+    constexpr int BS = NSF * NSF;
+    constexpr int OPT = pull2_opt<T, NSF>();
+    const int chunk_out = kPull2Threads * OPT;
+    const int2 *items = chunk_out == 128 ? pl->items128 : pl->items64;
+    const int64_t n_items = chunk_out == 128 ? pl->n_items128 : pl->n_items64;
+    if (n_items == 0) return LNV_OK;
+    const lnv_pattern *PA = pl->A, *PB = pl->B, *PC = pl->C;
+    size_t per_k = BS * sizeof(T) + sizeof(int32_t);
+    int kchunk = (int)std::min<size_t>((16 * 1024) / per_k, (size_t)std::max(pl->max_a_row, 1));
+    kchunk = std::max(kchunk, 1);
+    size_t smem = (size_t)kchunk * per_k + 16;
+    auto kern = k_pull2<T, NSF, OPT, TA, TB>;
+    if (smem > 48 * 1024)
+        LNV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)n_items, kPull2Threads, smem, ctx->stream>>>(
+        items, PA->row_ptr, PA->col, PA->tr, (const T *)A, PB->row_ptr, PB->col, PB->tr,
+        (const T *)B, PC->row_ptr, PC->col, (T *)C, chunk_out, kchunk);
+    LNV_LAUNCHED();
+    return LNV_OK;
+}
+
 template <typename T, int NSF, bool TA, bool TB>
 lnv_status dispatch_mode(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
                          const void *B2, void *C1, void *C2)
 {
+    if (pl->mode >= 3) {
+        if (B2) return launch_group<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
+        return launch_group<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr);
+    }
+    if (pl->mode == 2) {
+        LNV_TRY((launch_pull2<T, NSF, TA, TB>(ctx, pl, A, B1, C1)));
+        if (B2) LNV_TRY((launch_pull2<T, NSF, TA, TB>(ctx, pl, A, B2, C2)));
+        return LNV_OK;
+    }
     if (pl->mode == 0) {
-        if (B2) return launch_push<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
-        return launch_push<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr);
+        if (B2) return launch_push2<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
+        return launch_push2<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr);
     }
     LNV_TRY((launch_pull<T, NSF, TA, TB>(ctx, pl, A, B1, C1)));
     if (B2) LNV_TRY((launch_pull<T, NSF, TA, TB>(ctx, pl, A, B2, C2)));

@@ -275,7 +275,7 @@ __global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *__restrict__ 
 }  // namespace
 
 // out must hold n+1 values.
-static lnv_status scan_exclusive(cudaStream_t st, const int64_t *in, int64_t n, int64_t *out)
+lnv_status scan_exclusive(cudaStream_t st, const int64_t *in, int64_t n, int64_t *out)
 {
     const int T = 1024;
     int64_t nb = (n + T - 1) / T;

@@ -55,6 +55,7 @@ def lib():
                 "lnv_pattern_destroy": [P],
                 "lnv_plan_product": [P, P, P, P, i32, PP],
                 "lnv_plan_info": [P, P, P],
+                "lnv_plan_set_kernel": [P, P, i32],
                 "lnv_plan_destroy": [P],
                 "lnv_bsr_multiply": [P, P, i32, i32, P, P, P],
                 "lnv_trace_product": [P, P, i32, i32, P, P, P, P],
@@ -67,6 +68,8 @@ def lib():
                 "lnv_system_profile": [P, i32],
                 "lnv_system_stage_ms": [P, P],
                 "lnv_system_stage_triples": [P, P],
+                "lnv_system_stage_kernels": [P, P],
+                "lnv_system_autotune": [P, P, P, P, P, i32, P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -240,7 +243,14 @@ class Plan:
         self.h = h
         t, m = ctypes.c_int64(), ctypes.c_int()
         _check(lib().lnv_plan_info(self.h, ctypes.byref(t), ctypes.byref(m)), "lnv_plan_info")
-        self.triples, self.mode = t.value, ("push", "pull")[m.value]
+        self.triples, self.mode = t.value, self.KERNELS[m.value]
+
+    KERNELS = ("push", "pull", "pull-merge", "group", "group-sparse", "group-pipe", "group-mma")
+
+    def set_kernel(self, kernel):
+        k = self.KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)
+        _check(lib().lnv_plan_set_kernel(self.ctx.h, self.h, k), "lnv_plan_set_kernel")
+        self.mode = self.KERNELS[k]
 
     def multiply(self, A_vals, B_vals, C_vals=None, nsf=None, prec=None):
         nsf = nsf or A_vals.shape[-1]
@@ -361,6 +371,25 @@ class System:
 
     def profile(self, enable: bool = True):
         _check(lib().lnv_system_profile(self.h, int(enable)), "lnv_system_profile")
+
+    def stage_kernels(self) -> dict:
+        """Kernel chosen for each product stage."""
+        k = (ctypes.c_int * 7)()
+        _check(lib().lnv_system_stage_kernels(self.h, k), "lnv_system_stage_kernels")
+        return {s_: Plan.KERNELS[v] for s_, v in zip(self.STAGES, list(k)) if v >= 0}
+
+    def autotune(self, S, H, L, reps: int = 3) -> dict:
+        """Time every applicable kernel per product stage on these inputs and
+        keep the fastest; returns {stage: (kernel, ms)}."""
+        s = _vals(S, self.P_sh, self.nsf, self.prec, "S")
+        h = _vals(H, self.P_sh, self.nsf, self.prec, "H")
+        l_ = _vals(L, self.P_l, self.nsf, self.prec, "L")
+        ms = (ctypes.c_double * 35)()
+        _check(lib().lnv_system_autotune(self.ctx.h, self.h, s, h, l_, int(reps), ms), "lnv_system_autotune")
+        ks = self.stage_kernels()
+        self.tune_table = {st: {Plan.KERNELS[k]: ms[i * 7 + k] for k in range(7) if ms[i * 7 + k] >= 0}
+                           for i, st in enumerate(("XY", "TU", "Z", "Q", "W"))}
+        return {st: (ks[st], self.tune_table[st][ks[st]]) for st in self.tune_table}
 
     def stage_triples(self) -> dict:
         """Contributing block triples of each stage."""

@@ -108,10 +108,12 @@ PRODUCT_CASES = [
 ]
 
 
+@pytest.mark.parametrize("kernel", ["default", "push", "pull", "pull-merge", "group", "group-sparse",
+                                    "group-pipe", "group-mma"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("nsf", [1, 2, 4, 9])
 @pytest.mark.parametrize("case", PRODUCT_CASES)
-def test_masked_product_matches_oracle(ctx, dtype, nsf, case):
+def test_masked_product_matches_oracle(ctx, dtype, nsf, case, kernel):
     ra, rb, rc, ta, tb = case
     rng = np.random.default_rng(nsf * 7 + int(ta) + 2 * int(tb))
     ncell = 3 if nsf < 9 else 2
@@ -122,6 +124,8 @@ def test_masked_product_matches_oracle(ctx, dtype, nsf, case):
     B = oracle.csr(*ob, rng.standard_normal((ob[1].size, nsf, nsf)))
     A, B = rounded(A, dtype), rounded(B, dtype)
     plan = Plan(ctx, PA, PB, PC, trans_a=ta, trans_b=tb)
+    if kernel != "default":
+        plan.set_kernel(kernel)
     C = plan.multiply(to_dev(A["val"], dtype, ctx.device), to_dev(B["val"], dtype, ctx.device))
     ref = oracle.mprod(oracle.transpose(A) if ta else A, oracle.transpose(B) if tb else B, oc)
     err = rel_fro(C.cpu().numpy(), ref["val"])
@@ -132,10 +136,21 @@ def test_masked_product_matches_oracle(ctx, dtype, nsf, case):
 def test_plan_modes_follow_symbolic_counts(ctx):
     pos, cell = synth.si_diamond_positions(4, np.random.default_rng(0))
     P = {r: Pattern.build(ctx, pos, cell, r) for r in (6.6, 8.0, 14.6, 21.2)}
-    assert Plan(ctx, P[8.0], P[6.6], P[14.6]).mode == "push"
-    assert Plan(ctx, P[6.6], P[14.6], P[21.2]).mode == "push"
-    assert Plan(ctx, P[8.0], P[21.2], P[14.6]).mode == "pull"
-    assert Plan(ctx, P[14.6], P[21.2], P[8.0], True, True).mode == "pull"
+    # full-range products mostly miss on the dense table: hit lists
+    assert Plan(ctx, P[8.0], P[6.6], P[14.6]).mode == "group-sparse"
+    # masked products mostly hit: dense position table
+    assert Plan(ctx, P[14.6], P[21.2], P[8.0], True, True).mode == "group"
+    # a non-symmetric B pattern keeps the binary-search pull
+    rp, col = P[21.2].row_ptr.cpu().numpy(), P[21.2].col.cpu().numpy()
+    keep = col != np.repeat(np.arange(len(rp) - 1), np.diff(rp)) + 1  # drop (i, i+1) blocks
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))[keep]
+    nrp = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=len(rp) - 1))])
+    PB = Pattern.from_csr(ctx, nrp, col[keep])
+    assert not PB.symmetric
+    pl = Plan(ctx, P[8.0], PB, P[14.6])
+    with pytest.raises(LnvError) as e:
+        pl.set_kernel("pull-merge")
+    assert e.value.status == -5
 
 
 def test_product_empty_and_ragged_rows(ctx):
@@ -230,6 +245,19 @@ def test_lnv_4096_atoms_full(ctx, si4096, dtype):
     w, ref = si4096
     _, out, G = _gpu_lnv(ctx, w, dtype)
     _check_lnv(out, G, ref, dtype)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_autotuned_system_matches_oracle(ctx, dtype):
+    """After the autotuner picks a kernel per product, results still match."""
+    w, S, H, L = workload(3, 4, 6.6, 8.0, seed=31)
+    sysm = System(ctx, 4, PREC[dtype], w["pos"], w["cell"], 6.6, 8.0)
+    Sd, Hd, Ld = (to_dev(w[k], dtype, ctx.device) for k in ("S", "H", "L"))
+    tuned = sysm.autotune(Sd, Hd, Ld, reps=1)
+    assert set(tuned) == {"XY", "TU", "Z", "Q", "W"}
+    out, G = sysm.energy_grad(Sd, Hd, Ld)
+    ref = oracle_lnv(w, rounded(S, dtype), rounded(H, dtype), rounded(L, dtype))
+    _check_lnv(out.cpu().numpy(), G.cpu().numpy(), ref, dtype)
 
 
 def test_energy_only_matches_gradient_run(ctx):
