@@ -45,7 +45,23 @@ def parse():
     ap.add_argument("--impl", default="lnv", choices=["lnv", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the secondary FP64 measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels", default="",
+                    help="pin product kernels instead of autotuning, e.g. "
+                         "fp32:XY=group-sparse,TU=group;fp64:XY=push (as chosen by the autotuner)")
     return ap.parse_args()
+
+
+def pinned(spec: str, prec: str):
+    """{stage: kernel} for one precision from --kernels."""
+    out = {}
+    for part in filter(None, spec.split(";")):
+        p, _, body = part.partition(":")
+        if p != prec:
+            continue
+        for kv in filter(None, body.split(",")):
+            st, _, k = kv.partition("=")
+            out[st] = k
+    return out
 
 
 # ---------------------------------------------------------------- clocks
@@ -151,7 +167,7 @@ def build_inputs(ctx, dtype, seed_shift=0):
     return w, dev
 
 
-def time_path(ctx, w, prec, steps, warmup, dist, clocks=None):
+def time_path(ctx, w, prec, steps, warmup, dist, kernels=None):
     """Device-timed steps of one precision path; returns a result dict."""
     import torch
 
@@ -160,7 +176,12 @@ def time_path(ctx, w, prec, steps, warmup, dist, clocks=None):
     dtype = torch.float32 if prec == "fp32" else torch.float64
     sysm = System(ctx, NSF, prec, w["pos"], w["cell"], R_SH, R_L)
     S, H, L = (torch.from_numpy(w[k]).to(ctx.device, dtype) for k in ("S", "H", "L"))
-    tuned = sysm.autotune(S, H, L, reps=2)  # setup: kernel choice per product, untimed
+    if kernels:
+        for st, k in kernels.items():
+            sysm.set_stage_kernel(st, k)
+        tuned = {st: (k, None) for st, k in sysm.stage_kernels().items()}
+    else:
+        tuned = sysm.autotune(S, H, L, reps=2)  # setup: kernel choice per product, untimed
     out = torch.empty((1, 6), dtype=torch.float64, device=ctx.device)
     G = torch.empty_like(L)
     ws = torch.empty(sysm.workspace_size(True), dtype=torch.uint8, device=ctx.device)
@@ -358,8 +379,9 @@ def main():
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
     clocks = Clocks(gpu_id)
     clocks.start()
-    r32 = time_path(ctx, w, "fp32", args.steps, args.warmup, dist)
-    r64 = None if args.no_fp64 else time_path(ctx, w, "fp64", args.steps, args.warmup, dist)
+    r32 = time_path(ctx, w, "fp32", args.steps, args.warmup, dist, pinned(args.kernels, "fp32"))
+    r64 = None if args.no_fp64 else time_path(ctx, w, "fp64", args.steps, args.warmup, dist,
+                                              pinned(args.kernels, "fp64"))
     clocks.stop()
     e2e32 = e2e(ctx, r32, args.steps, args.warmup)
 

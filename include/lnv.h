@@ -203,6 +203,10 @@ lnv_status lnv_system_destroy(lnv_system *sys);
  * in the numbering of lnv_plan_info. */
 lnv_status lnv_system_stage_kernels(const lnv_system *sys, int *k7);
 
+/* Select the kernel of one product stage (0 XY, 1 TU, 2 Z, 4 Q, 5 W) by
+ * hand, in the numbering of lnv_plan_info; as lnv_plan_set_kernel. */
+lnv_status lnv_system_set_stage_kernel(lnv_ctx *ctx, lnv_system *sys, int stage, int kernel);
+
 /* Autotuner: runs one evaluation on S, H, L, then times every applicable
  * kernel of each product stage (XY, TU, Z, Q, W) on those intermediates
  * (reps launches each, CUDA events on the context stream) and keeps the

@@ -383,6 +383,16 @@ lnv_status lnv_system_stage_kernels(const lnv_system *sys, int *k7)
     return LNV_OK;
 }
 
+lnv_status lnv_system_set_stage_kernel(lnv_ctx *ctx, lnv_system *sys, int stage, int kernel)
+{
+    LNV_TRY(set_dev(ctx));
+    LNV_ARG(sys, "null system");
+    lnv_plan *pl = stage == 0 ? sys->pl_xy : stage == 1 ? sys->pl_tu : stage == 2 ? sys->pl_z
+                 : stage == 4 ? sys->pl_q : stage == 5 ? sys->pl_w : nullptr;
+    LNV_ARG(pl, "stage must be 0 (XY), 1 (TU), 2 (Z), 4 (Q) or 5 (W)");
+    return plan_set_kernel(ctx, pl, kernel);
+}
+
 lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev, const void *H_dev,
                                const void *L_dev, int reps, double *ms_out)
 {

@@ -70,6 +70,7 @@ def lib():
                 "lnv_system_stage_triples": [P, P],
                 "lnv_system_stage_kernels": [P, P],
                 "lnv_system_autotune": [P, P, P, P, P, i32, P],
+                "lnv_system_set_stage_kernel": [P, P, i32, i32],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -377,6 +378,12 @@ class System:
         k = (ctypes.c_int * 7)()
         _check(lib().lnv_system_stage_kernels(self.h, k), "lnv_system_stage_kernels")
         return {s_: Plan.KERNELS[v] for s_, v in zip(self.STAGES, list(k)) if v >= 0}
+
+    def set_stage_kernel(self, stage: str, kernel):
+        """Pin the kernel of one product stage ("XY", "TU", "Z", "Q", "W")."""
+        k = Plan.KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)
+        _check(lib().lnv_system_set_stage_kernel(self.ctx.h, self.h, self.STAGES.index(stage), k),
+               "lnv_system_set_stage_kernel")
 
     def autotune(self, S, H, L, reps: int = 3) -> dict:
         """Time every applicable kernel per product stage on these inputs and
