@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--impl", default="lnv", choices=["lnv", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the secondary FP64 measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="si4096",
+                    choices=["si4096", "batch64", "si32768_nsf9", "si32768_autograd"],
+                    help="si4096: the benchmark workload; the others are the batched, NSF=9 and "
+                         "autograd workloads, reported on their own JSON line")
     ap.add_argument("--kernels", default="",
                     help="pin product kernels instead of autotuning, e.g. "
                          "fp32:XY=group-sparse,TU=group;fp64:XY=push (as chosen by the autotuner)")
@@ -352,6 +356,137 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def _flush_timed(ctx, fn, steps, warmup):
+    """CUDA-event time of `steps` calls of fn (L2 flushed before each, outside
+    the events), after `warmup` calls; returns seconds."""
+    import torch
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=ctx.device)
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(ctx.stream)
+        fn()
+        b.record(ctx.stream)
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b) / 1e3
+    return total
+
+
+def run_batch64(args, ctx):
+    """64 independent Si supercells (n^3 cells, n uniform in 2..10, seeds
+    1000+s) evaluated together: one block-diagonal system, autotuned, one CUDA
+    graph replay per step; against per-system launches of the same systems."""
+    import gc
+
+    import torch
+
+    import synth
+    from paper_0911_3584_gb300 import Pattern, System
+
+    def pattern_fn(pos, cell, R):
+        P = Pattern.build(ctx, pos, cell, R)
+        return P.row_ptr.cpu().numpy(), P.col.cpu().numpy()
+
+    counts = synth.batch_cell_counts(64, 2, 10, 0)
+    ws = [synth.si_workload(n, NSF, R_SH, R_L, 1000 + s_, pattern_fn) for s_, n in enumerate(counts)]
+    off = [0]
+    for w in ws:
+        off.append(off[-1] + w["pos"].shape[0])
+    n_atoms = off[-1]
+    dt = torch.float32
+    sysb = System(ctx, NSF, "fp32", np.concatenate([w["pos"] for w in ws]), [w["cell"] for w in ws],
+                  R_SH, R_L, seg_off=off)
+    S, H, L = (torch.from_numpy(np.concatenate([w[k] for w in ws])).to(ctx.device, dt) for k in ("S", "H", "L"))
+    tuned = sysb.autotune(S, H, L, reps=2)
+    graph, out, G = sysb.capture(S, H, L)
+    t_graph = _flush_timed(ctx, graph.replay, args.steps, args.warmup)
+    flops = 2 * NSF ** 3 * sysb.triples(True)
+    del graph, sysb, S, H, L, out, G
+    gc.collect()
+    torch.cuda.empty_cache()
+    # per-system launches: each system on its own, autotuned the same way
+    t_sep = 0.0
+    for w in ws:
+        sy = System(ctx, NSF, "fp32", w["pos"], w["cell"], R_SH, R_L)
+        Ss, Hs, Ls = (torch.from_numpy(w[k]).to(ctx.device, dt) for k in ("S", "H", "L"))
+        sy.autotune(Ss, Hs, Ls, reps=1)
+        t_sep += _flush_timed(ctx, lambda: sy.energy_grad(Ss, Hs, Ls), args.steps, args.warmup)
+        del sy, Ss, Hs, Ls
+        gc.collect()
+        torch.cuda.empty_cache()
+    line = {
+        "metric": METRIC, "value": round(n_atoms * args.steps / t_graph, 1), "unit": "atoms/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_graph * 1e3 / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch64_si_cells2to10_nsf4_rsh6.6A_rl8A", "systems": 64, "atoms": n_atoms,
+                   "cell_counts": counts, "mode": "one block-diagonal evaluation replayed as a CUDA graph",
+                   "l2": "flushed between timed steps"},
+        "gflops": round(flops * args.steps / t_graph / 1e9, 1),
+        "stage_kernels": {k: v[0] for k, v in tuned.items()},
+        "per_system_launches": {"value": round(n_atoms * args.steps / t_sep, 1), "unit": "atoms/s",
+                                "ms_per_step": round(t_sep * 1e3 / args.steps, 4)},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_large(args, ctx, nsf, r_l, autograd):
+    """32768-atom Si (16^3 cells).  nsf=9, R_L=10: FP32 products with FP64 traces.
+    autograd: NSF=4, R_L=10, FP32 storage, E(L) through the recompute-backward
+    autograd function (forward + backward per step), peak memory reported."""
+    import torch
+
+    import synth
+    from paper_0911_3584_gb300 import Pattern, System, lnv_energy
+
+    def pattern_fn(pos, cell, R):
+        P = Pattern.build(ctx, pos, cell, R)
+        return P.row_ptr.cpu().numpy(), P.col.cpu().numpy()
+
+    w = synth.si_workload(16, nsf, R_SH, r_l, SEED, pattern_fn)
+    n_atoms = w["pos"].shape[0]
+    dt = torch.float32
+    sysm = System(ctx, nsf, "fp32", w["pos"], w["cell"], R_SH, r_l)
+    S, H, L = (torch.from_numpy(w[k]).to(ctx.device, dt) for k in ("S", "H", "L"))
+    del w
+    tuned = sysm.autotune(S, H, L, reps=1)
+    torch.cuda.reset_peak_memory_stats(ctx.device)
+    base_alloc = torch.cuda.memory_allocated(ctx.device)
+    if autograd:
+        Lg = L.clone().requires_grad_(True)
+
+        def step():
+            Lg.grad = None
+            E, _ = lnv_energy(Lg, sysm, S, H)
+            E.backward()
+    else:
+        out = torch.empty((1, 6), dtype=torch.float64, device=ctx.device)
+        G = torch.empty_like(L)
+
+        def step():
+            sysm.energy_grad(S, H, L, out=out, G=G)
+    t = _flush_timed(ctx, step, args.steps, args.warmup)
+    peak = torch.cuda.max_memory_allocated(ctx.device)
+    flops = 2 * nsf ** 3 * (sysm.triples(True) + (sysm.triples(False) if autograd else 0))
+    line = {
+        "metric": METRIC, "value": round(n_atoms * args.steps / t, 1), "unit": "atoms/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"si_diamond_16x16x16_32768atoms_nsf{nsf}_rsh6.6A_rl{r_l:g}A",
+                   "atoms": n_atoms, "nsf": nsf, "r_l": r_l,
+                   "step": "autograd forward + recompute backward" if autograd else "energy + gradient"},
+        "gflops": round(flops * args.steps / t / 1e9, 1),
+        "stage_kernels": {k: v[0] for k, v in tuned.items()},
+        "memory": {"library_workspace_bytes": sysm.workspace_size(True),
+                   "torch_peak_bytes_during_steps": int(peak), "torch_bytes_before_steps": int(base_alloc)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -374,6 +509,14 @@ def main():
         dist = tdist
     dev = torch.device("cuda", local)
     ctx = Context(dev)
+    if args.config != "si4096":
+        if args.config == "batch64":
+            run_batch64(args, ctx)
+        elif args.config == "si32768_nsf9":
+            run_large(args, ctx, 9, 10.0, False)
+        else:
+            run_large(args, ctx, 4, 10.0, True)
+        return
     w, _ = build_inputs(ctx, torch.float64)
     props = torch.cuda.get_device_properties(dev)
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)

@@ -135,7 +135,7 @@ lnv_status lnv_plan_product(lnv_ctx *ctx, const lnv_pattern *A, const lnv_patter
  * a hi/lo split of both operands, FP32 accumulation; FP32 values, NSF = 4;
  * other cases run kernel 3).
  * The default is 3 when at least half of the table's candidates hit, else 4,
- * when the tables fit a quarter of the free device memory. */
+ * when the tables fit a third of the free device memory. */
 lnv_status lnv_plan_info(const lnv_plan *plan, int64_t *triples, int *mode);
 /* Select the kernel of a plan (0..6 as above); all give the same result up
  * to rounding order.  Kernels 3-5 build their tables on first selection

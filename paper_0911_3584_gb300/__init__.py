@@ -3,6 +3,7 @@
 Bowler & Miyazaki (CONQUEST), Sec. 2: K = 3LSL - 2LSLSL (Eq. 3), N_e = 2 Tr[KS],
 band energy E = 2 Tr[KH] and its gradient with respect to the range-truncated
 auxiliary density matrix L.  The computation runs in liblnv (CUDA, sm_103a)
+from .autograd import LNVEnergy, lnv_energy  # noqa: F401
 behind the C ABI of include/lnv.h; this package is its Python binding.
 """
 from .lnv import (  # noqa: F401
@@ -18,3 +19,4 @@ from .lnv import (  # noqa: F401
     trace_product,
     version,
 )
+from .autograd import LNVEnergy, lnv_energy  # noqa: F401

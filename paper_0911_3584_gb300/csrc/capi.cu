@@ -13,6 +13,9 @@
 // vanishes beyond R_A + R_B), and Z is needed only inside R_X.
 #include <atomic>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <cstdarg>
 #include <cstring>
 #include <new>
@@ -25,6 +28,22 @@ static thread_local char g_err[512] = "";
 static std::atomic<int64_t> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaError_t ensure_smem(const void *kernel, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> set;  // (kernel, device) -> bytes
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const std::pair<const void *, int> key(kernel, dev);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = set.find(key);
+    if (it != set.end() && it->second >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) set[key] = bytes;
+    return e;
+}
 
 void set_error(const char *fmt, ...)
 {
@@ -463,6 +482,7 @@ lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
         }
         if (st == LNV_OK) st = plan_set_kernel(ctx, sg.pl, best);
         else plan_set_kernel(ctx, sg.pl, orig);
+        if (st == LNV_OK) plan_trim(sg.pl);
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

@@ -115,8 +115,8 @@ void group_plan_free(GroupPlan *gp)
     *gp = GroupPlan();
 }
 
-lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes, bool dense,
-                            bool sparse)
+// Lists (K, J, apos, cpos) and hit counts of the row groups: built once per plan.
+static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes)
 {
     const lnv_pattern *A = pl->A, *B = pl->B, *C = pl->C;
     if (B->max_row >= 0xFFFF) {
@@ -127,7 +127,6 @@ lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_byt
     LNV_TRY(pattern_host_cols(ctx, C));
     const int64_t n = C->n;
     const int64_t ng = (n + G - 1) / G;
-    // sizes first (unions per group), in parallel over groups
     std::vector<int64_t> nk(ng), nj(ng);
     std::vector<std::vector<int32_t>> Ks(ng), Js(ng);
     auto unite = [&](const lnv_pattern *P, int64_t r0, int64_t r1, std::vector<int32_t> &out) {
@@ -161,10 +160,9 @@ lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_byt
         max_k = std::max<int>(max_k, (int)nk[g]);
         max_j = std::max<int>(max_j, (int)nj[g]);
     }
-    const size_t need = (dense ? sizeof(uint16_t) * (size_t)b_off[ng] : 0) +
-                        (sizeof(int32_t) * (1 + G)) * (size_t)(k_off[ng] + j_off[ng]);
+    const size_t need = (sizeof(int32_t) * (1 + G) + sizeof(int64_t)) * (size_t)(k_off[ng] + j_off[ng]);
     if (need > budget_bytes) {
-        set_error("row-group plan needs %zu bytes, over the %zu budget", need, budget_bytes);
+        set_error("row-group lists need %zu bytes, over the %zu budget", need, budget_bytes);
         return LNV_ERR_UNSUPPORTED;
     }
     std::vector<int32_t> k_list(k_off[ng]), j_list(j_off[ng]);
@@ -199,6 +197,7 @@ lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_byt
     gp.n_groups = ng;
     gp.max_k = max_k;
     gp.max_j = max_j;
+    gp.candidates = b_off[ng];
     size_t bytes = 0;
     lnv_status s = LNV_OK;
     if (s == LNV_OK) s = upload(k_off, &gp.k_off, &bytes);
@@ -208,28 +207,8 @@ lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_byt
     if (s == LNV_OK) s = upload(j_list, &gp.j_list, &bytes);
     if (s == LNV_OK) s = upload(cpos, &gp.cpos, &bytes);
     if (s == LNV_OK) s = upload(b_off, &gp.bidx_off, &bytes);
-    gp.candidates = b_off[ng];
-    if (s == LNV_OK && dense && b_off[ng] > 0) {
-        cudaError_t e = cudaMalloc(&gp.bidx, sizeof(uint16_t) * (size_t)b_off[ng]);
-        if (e != cudaSuccess) {
-            set_error("row-group plan: %s", cudaGetErrorString(e));
-            s = e == cudaErrorMemoryAllocation ? LNV_ERR_OOM : LNV_ERR_CUDA;
-        } else {
-            bytes += sizeof(uint16_t) * (size_t)b_off[ng];
-            e = cudaMemsetAsync(gp.bidx, 0xFF, sizeof(uint16_t) * (size_t)b_off[ng], ctx->stream);
-            k_bidx<<<(unsigned)ng, 256, 0, ctx->stream>>>(gp.k_off, gp.k_list, gp.j_off, gp.j_list,
-                                                          gp.bidx_off, B->row_ptr, B->col, pl->trans_b, gp.bidx);
-            count_launch();
-            e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-            if (e != cudaSuccess) {
-                set_error("row-group position table: %s", cudaGetErrorString(e));
-                s = LNV_ERR_CUDA;
-            }
-        }
-    }
-    if (s == LNV_OK && sparse && j_off[ng] > 0) {
-        // count, scan, fill
+    // hit counts per (group, j) -> offsets of the hit lists
+    if (s == LNV_OK && j_off[ng] > 0) {
         int64_t *cnt = nullptr;
         cudaError_t e = cudaMalloc(&cnt, sizeof(int64_t) * (size_t)j_off[ng]);
         if (e == cudaSuccess) e = cudaMalloc(&gp.hoff, sizeof(int64_t) * (size_t)(j_off[ng] + 1));
@@ -241,24 +220,13 @@ lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_byt
         }
         if (e == cudaSuccess) {
             s = scan_exclusive(ctx->stream, cnt, j_off[ng], gp.hoff);
-            if (s == LNV_OK) {
+            if (s == LNV_OK)
                 e = cudaMemcpy(&gp.hits, gp.hoff + j_off[ng], sizeof(int64_t), cudaMemcpyDeviceToHost);
-                if (e == cudaSuccess && gp.hits > 0) e = cudaMalloc(&gp.hk, sizeof(uint16_t) * (size_t)gp.hits);
-                if (e == cudaSuccess && gp.hits > 0) e = cudaMalloc(&gp.hp, sizeof(int32_t) * (size_t)gp.hits);
-                if (e == cudaSuccess && gp.hits > 0) {
-                    k_hits<<<(unsigned)ng, 128, 0, ctx->stream>>>(gp.k_off, gp.k_list, gp.j_off, gp.j_list,
-                                                                 B->row_ptr, B->col, pl->trans_b, nullptr,
-                                                                 gp.hoff, gp.hk, gp.hp);
-                    count_launch();
-                    e = cudaGetLastError();
-                }
-                if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-                bytes += sizeof(int64_t) * (size_t)(j_off[ng] + 1) + 6 * (size_t)gp.hits;
-            }
+            bytes += sizeof(int64_t) * (size_t)(j_off[ng] + 1);
         }
         cudaFree(cnt);
         if (s == LNV_OK && e != cudaSuccess) {
-            set_error("row-group hit lists: %s", cudaGetErrorString(e));
+            set_error("row-group hit counts: %s", cudaGetErrorString(e));
             s = e == cudaErrorMemoryAllocation ? LNV_ERR_OOM : LNV_ERR_CUDA;
         }
     }
@@ -267,6 +235,46 @@ lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_byt
         return s;
     }
     gp.bytes = bytes;
+    return LNV_OK;
+}
+
+// Build the lists (once) and the requested forms: the dense 16-bit position
+// table and / or the hit lists.  Each form is checked against the budget.
+lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes, bool dense,
+                            bool sparse)
+{
+    GroupPlan &gp = pl->grp;
+    if (gp.G == 0) LNV_TRY(group_plan_lists(ctx, pl, G, budget_bytes));
+    const lnv_pattern *B = pl->B;
+    const int64_t ng = gp.n_groups;
+    if (dense && !gp.bidx && gp.candidates > 0) {
+        const size_t need = sizeof(uint16_t) * (size_t)gp.candidates;
+        if (need > budget_bytes) {
+            set_error("row-group position table needs %zu bytes, over the %zu budget", need, budget_bytes);
+            return LNV_ERR_UNSUPPORTED;
+        }
+        LNV_CUDA(cudaMalloc(&gp.bidx, need));
+        LNV_CUDA(cudaMemsetAsync(gp.bidx, 0xFF, need, ctx->stream));
+        k_bidx<<<(unsigned)ng, 256, 0, ctx->stream>>>(gp.k_off, gp.k_list, gp.j_off, gp.j_list, gp.bidx_off,
+                                                      B->row_ptr, B->col, pl->trans_b, gp.bidx);
+        LNV_LAUNCHED();
+        LNV_CUDA(cudaStreamSynchronize(ctx->stream));
+        gp.bytes += need;
+    }
+    if (sparse && !gp.hk && gp.hits > 0) {
+        const size_t need = (sizeof(uint16_t) + sizeof(int32_t)) * (size_t)gp.hits;
+        if (need > budget_bytes) {
+            set_error("row-group hit lists need %zu bytes, over the %zu budget", need, budget_bytes);
+            return LNV_ERR_UNSUPPORTED;
+        }
+        LNV_CUDA(cudaMalloc(&gp.hk, sizeof(uint16_t) * (size_t)gp.hits));
+        LNV_CUDA(cudaMalloc(&gp.hp, sizeof(int32_t) * (size_t)gp.hits));
+        k_hits<<<(unsigned)ng, 128, 0, ctx->stream>>>(gp.k_off, gp.k_list, gp.j_off, gp.j_list, B->row_ptr, B->col,
+                                                     pl->trans_b, nullptr, gp.hoff, gp.hk, gp.hp);
+        LNV_LAUNCHED();
+        LNV_CUDA(cudaStreamSynchronize(ctx->stream));
+        gp.bytes += need;
+    }
     return LNV_OK;
 }
 

@@ -49,6 +49,10 @@ void count_launch();
 // Maximum blocks in one pattern row (bitonic row sort in shared memory).
 constexpr int kMaxRow = 16384;
 
+// Raise a kernel's dynamic shared-memory limit once (not inside every launch,
+// so that launches can be captured in CUDA graphs).
+cudaError_t ensure_smem(const void *kernel, size_t bytes);
+
 }  // namespace lnv
 
 struct lnv_ctx {
@@ -131,6 +135,8 @@ lnv_status pattern_submap(lnv_ctx *ctx, const lnv_pattern *sub, const lnv_patter
 lnv_status plan_create(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
                        const lnv_pattern *C, int flags, lnv_plan **out);
 void plan_free(lnv_plan *plan);
+// Free the row-group tables the plan's current kernel does not use.
+void plan_trim(lnv_plan *plan);
 lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel);
 // Row-group plan (group.cu); returns LNV_ERR_UNSUPPORTED when the table would
 // not fit the budget or a B row is too long for 16-bit offsets.

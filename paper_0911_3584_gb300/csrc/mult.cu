@@ -129,15 +129,18 @@ lnv_status plan_create(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
     pl->pull_cand = (int64_t)h[2];
     pl->mode = pl->push_scan <= pl->pull_cand ? 0 : (B->symmetric ? 2 : 1);
     {
-        // Prefer the row-group kernel when its position table fits: a quarter of
-        // the free device memory, at most 16 GB.
+        // Prefer the row-group kernels when their tables fit a third of the free
+        // device memory.
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
-        const size_t budget = std::min<size_t>(free_b / 4, (size_t)16 << 30);
-        lnv_status gs = group_plan_build(ctx, pl, 4, budget, true, true);
+        const size_t budget = free_b / 3;
+        lnv_status gs = group_plan_build(ctx, pl, 4, budget, false, false);
         // dense position table when most candidates hit, hit lists otherwise
-        if (gs == LNV_OK)
-            pl->mode = (pl->grp.candidates > 0 && 2 * pl->grp.hits >= pl->grp.candidates) ? 3 : 4;
+        if (gs == LNV_OK) {
+            const bool dense = pl->grp.candidates > 0 && 2 * pl->grp.hits >= pl->grp.candidates;
+            gs = group_plan_build(ctx, pl, 4, budget, dense, !dense);
+            if (gs == LNV_OK) pl->mode = dense ? 3 : 4;
+        }
         else if (gs != LNV_ERR_UNSUPPORTED) {
             plan_free(pl);
             return gs;
@@ -199,14 +202,32 @@ lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
         }
         LNV_TRY(plan_pull_items(pl));
     }
-    if (((kernel == 3 || kernel == 5 || kernel == 6) && !pl->grp.bidx) || (kernel == 4 && !pl->grp.hoff)) {
-        group_plan_free(&pl->grp);
+    if (kernel >= 3) {
+        // build the row-group form this kernel reads, if missing
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
-        LNV_TRY(group_plan_build(ctx, pl, 4, std::min<size_t>(free_b / 4, (size_t)16 << 30), true, true));
+        LNV_TRY(group_plan_build(ctx, pl, 4, free_b / 3, kernel != 4, kernel == 4));
     }
     pl->mode = kernel;
     return LNV_OK;
+}
+
+void plan_trim(lnv_plan *plan)
+{
+    GroupPlan &gp = plan->grp;
+    const bool dense = plan->mode == 3 || plan->mode == 5 || plan->mode == 6, sparse = plan->mode == 4;
+    if (!dense && !sparse) {
+        group_plan_free(&gp);
+        return;
+    }
+    if (!dense && gp.bidx) {
+        cudaFree(gp.bidx);
+        gp.bidx = nullptr;
+    }
+    if (!sparse && gp.hk) {
+        cudaFree(gp.hk); cudaFree(gp.hp);
+        gp.hk = nullptr; gp.hp = nullptr;
+    }
 }
 
 void plan_free(lnv_plan *plan)

@@ -1160,7 +1160,7 @@ lnv_status launch_push(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const vo
     }
     size_t smem = (size_t)NOUT * chunk * BS * sizeof(T) + BS * sizeof(T) + sizeof(int32_t) * chunk + 16;
     auto kern = k_push<T, NSF, NOUT, TA, TB>;
-    LNV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LNV_CUDA(ensure_smem((const void *)kern, smem));
     kern<<<(unsigned)PC->n, kThreads, smem, ctx->stream>>>(
         PA->row_ptr, PA->col, PA->tr, (const T *)A, PB->row_ptr, PB->col, PB->tr, (const T *)B1,
         (const T *)B2, PC->row_ptr, PC->col, (T *)C1, (T *)C2, chunk);
@@ -1180,7 +1180,7 @@ lnv_status launch_pull(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const vo
     int kchunk = (int)std::min<size_t>(budget / per_k, (size_t)std::max(pl->max_a_row, 1));
     size_t smem = (size_t)kchunk * per_k + 16;
     auto kern = k_pull<T, NSF, OPT, TA, TB>;
-    LNV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LNV_CUDA(ensure_smem((const void *)kern, smem));
     kern<<<(unsigned)PC->n, kThreads, smem, ctx->stream>>>(
         PA->row_ptr, PA->col, PA->tr, (const T *)A, PB->row_ptr, PB->col, PB->tr, (const T *)B,
         PC->row_ptr, PC->col, (T *)C, kchunk);
@@ -1209,7 +1209,7 @@ lnv_status launch_grp(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const voi
     constexpr int OPT = NSF == 4 ? 2 : 1;
     const GroupPlan &gp = pl->grp;
     if (gp.n_groups == 0 || gp.max_j == 0) return LNV_OK;
-    if (SPARSE ? !gp.hoff : !gp.bidx) {
+    if (SPARSE ? (!gp.hk && gp.hits > 0) : (!gp.bidx && gp.candidates > 0)) {
         set_error("row-group plan lacks the %s", SPARSE ? "hit lists" : "position table");
         return LNV_ERR_UNSUPPORTED;
     }
@@ -1220,8 +1220,7 @@ lnv_status launch_grp(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const voi
                                                            (SPARSE ? 40 : 32) * 1024 / per_k));
     const size_t smem = (size_t)kchunk * per_k + 128;
     auto kern = k_grp<T, NSF, G, NOUT, CW, OPT, TA, TB, SPARSE>;
-    if (smem > 48 * 1024)
-        LNV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LNV_CUDA(ensure_smem((const void *)kern, smem));
     dim3 grid((unsigned)gp.n_groups, (unsigned)((gp.max_j + jc - 1) / jc));
     kern<<<grid, kGroupThreads, smem, ctx->stream>>>(
         gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list, gp.cpos, gp.bidx_off, gp.bidx, gp.hoff,
@@ -1240,7 +1239,7 @@ lnv_status launch_gpipe(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const v
     if (gp.n_groups == 0 || gp.max_j == 0) return LNV_OK;
     const size_t smem = sizeof(T) * (2 * KC * JC * BS + 2 * KC * G * BS) + sizeof(uint32_t) * 2 * KC + 64;
     auto kern = k_gpipe<T, G, KC, TA, TB>;
-    LNV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LNV_CUDA(ensure_smem((const void *)kern, smem));
     dim3 grid((unsigned)gp.n_groups, (unsigned)((gp.max_j + JC - 1) / JC));
     kern<<<grid, 128, smem, ctx->stream>>>(gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list,
                                           gp.cpos, gp.bidx_off, gp.bidx, pl->A->tr, (const T *)A,
@@ -1265,8 +1264,7 @@ lnv_status launch_gmma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const vo
     int kchunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(gp.max_k, 1), (32 * 1024) / per_k));
     const size_t smem = (size_t)kchunk * per_k + 128;
     auto kern = k_gmma<NOUT, NT, TA, TB>;
-    if (smem > 48 * 1024)
-        LNV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LNV_CUDA(ensure_smem((const void *)kern, smem));
     dim3 grid((unsigned)gp.n_groups, (unsigned)((gp.max_j + JC - 1) / JC));
     kern<<<grid, 128, smem, ctx->stream>>>(gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list, gp.cpos,
                                           gp.bidx_off, gp.bidx, pl->A->tr, (const float *)A,
@@ -1324,7 +1322,7 @@ lnv_status launch_push2(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const v
     size_t smem = (size_t)NOUT * chunk * BS * sizeof(T) + (size_t)kchunk * BS * sizeof(T) +
                   sizeof(int32_t) * ((size_t)chunk + (size_t)kchunk * (NW + 1) + kchunk) + 16;
     auto kern = k_push2<T, NSF, NOUT, TA, TB, NW>;
-    LNV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LNV_CUDA(ensure_smem((const void *)kern, smem));
     dim3 grid((unsigned)PC->n, (unsigned)((PC->max_row + chunk - 1) / chunk));
     kern<<<grid, NW * 32, smem, ctx->stream>>>(
         PA->row_ptr, PA->col, PA->tr, (const T *)A, PB->row_ptr, PB->col, PB->tr, (const T *)B1,
@@ -1356,8 +1354,7 @@ lnv_status launch_pull2(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const v
     kchunk = std::max(kchunk, 1);
     size_t smem = (size_t)kchunk * per_k + 16;
     auto kern = k_pull2<T, NSF, OPT, TA, TB>;
-    if (smem > 48 * 1024)
-        LNV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LNV_CUDA(ensure_smem((const void *)kern, smem));
     kern<<<(unsigned)n_items, kPull2Threads, smem, ctx->stream>>>(
         items, PA->row_ptr, PA->col, PA->tr, (const T *)A, PB->row_ptr, PB->col, PB->tr,
         (const T *)B, PC->row_ptr, PC->col, (T *)C, chunk_out, kchunk);

@@ -370,6 +370,36 @@ class System:
 
     STAGES = ("XY", "TU", "Z", "traces", "Q", "W", "G")
 
+    def capture(self, S, H, L, grad: bool = True, out=None, G=None, workspace=None):
+        """Capture one evaluation in a CUDA graph; returns (graph, out, G).
+
+        graph.replay() re-runs every kernel of the evaluation on the current
+        contents of S, H, L (same device buffers) into out and G.  One warm-up
+        evaluation runs first (outside the capture) so that no allocation or
+        attribute change happens while capturing.
+        """
+        dev = self.ctx.device
+        if out is None:
+            out = torch.empty((self.n_seg, 6), dtype=torch.float64, device=dev)
+        if grad and G is None:
+            G = torch.empty_like(L)
+        if workspace is None:
+            workspace = torch.empty(self.workspace_size(grad), dtype=torch.uint8, device=dev)
+        self.profile(False)
+        self.energy_grad(S, H, L, grad=grad, out=out, G=G, workspace=workspace)
+        torch.cuda.synchronize(dev)
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        old = self.ctx.stream
+        with torch.cuda.graph(graph, stream=side):
+            self.ctx.set_stream(side)
+            try:
+                self.energy_grad(S, H, L, grad=grad, out=out, G=G, workspace=workspace)
+            finally:
+                self.ctx.set_stream(old)
+        self._graph_refs = (out, G, workspace)
+        return graph, out, G
+
     def profile(self, enable: bool = True):
         _check(lib().lnv_system_profile(self.h, int(enable)), "lnv_system_profile")
 

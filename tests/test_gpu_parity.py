@@ -329,3 +329,87 @@ def test_argument_errors(ctx):
     ws = torch.empty(16, dtype=torch.uint8, device=ctx.device)
     with pytest.raises(LnvError):
         sysm.energy_grad(Sd, Hd, Ld, workspace=ws)
+
+
+# ------------------------------------------------------------------ autograd (recompute backward)
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_autograd_energy_gradient_matches_oracle(ctx, dtype):
+    from paper_0911_3584_gb300 import lnv_energy
+    w, S, H, L = workload(2, 4, 6.6, 8.0, seed=41)
+    sysm = System(ctx, 4, PREC[dtype], w["pos"], w["cell"], 6.6, 8.0)
+    Sd, Hd = (to_dev(w[k], dtype, ctx.device) for k in ("S", "H"))
+    Ld = to_dev(w["L"], dtype, ctx.device).requires_grad_(True)
+    E, Ne = lnv_energy(Ld, sysm, Sd, Hd)
+    (3.0 * E).backward()
+    ref = oracle_lnv(w, rounded(S, dtype), rounded(H, dtype), rounded(L, dtype))
+    tm, ts = TOL[dtype]
+    assert abs(E.item() - ref["E"]) <= ts * abs(ref["E"])
+    assert abs(Ne.item() - ref["Ne"]) <= ts * abs(ref["Ne"])
+    assert rel_fro(Ld.grad.cpu().numpy(), 3.0 * ref["G"]) <= tm
+
+
+def test_autograd_gradient_against_central_differences(ctx):
+    """Central differences of E(L + tD) in FP64 (step 1e-6) on 20 random blocks
+    against <dE/dL, D> from the recompute backward."""
+    from paper_0911_3584_gb300 import lnv_energy
+    w, S, H, L = workload(3, 4, 6.6, 8.0, seed=43)
+    sysm = System(ctx, 4, "fp64", w["pos"], w["cell"], 6.6, 8.0)
+    Sd, Hd = (to_dev(w[k], torch.float64, ctx.device) for k in ("S", "H"))
+    L0 = to_dev(w["L"], torch.float64, ctx.device)
+    Lg = L0.clone().requires_grad_(True)
+    E, _ = lnv_energy(Lg, sysm, Sd, Hd)
+    E.backward()
+    G = Lg.grad
+    rp, col = w["l_row_ptr"], w["l_col"]
+    n = rp.size - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    key = rows * n + col
+    rng = np.random.default_rng(5)
+    h = 1e-6
+    for p in rng.choice(col.size, size=20, replace=False):
+        i, j = rows[p], col[p]
+        D = torch.zeros_like(L0)
+        blk = torch.from_numpy(rng.standard_normal((4, 4))).to(ctx.device)
+        if i == j:
+            blk = 0.5 * (blk + blk.T)
+        D[p] = blk
+        D[int(np.searchsorted(key, j * n + i))] = blk.T
+        ep = sysm.energy_grad(Sd, Hd, L0 + h * D, grad=False)[0][0, 0].item()
+        em = sysm.energy_grad(Sd, Hd, L0 - h * D, grad=False)[0][0, 0].item()
+        fd = (ep - em) / (2 * h)
+        an = float((G * D).sum())
+        # central differences of a cubic: error h^2 E'''/6 plus rounding eps |E| / h
+        assert fd == pytest.approx(an, rel=1e-6, abs=1e-7)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_graph_captured_batched_evaluation(ctx, dtype):
+    """Many systems in one block-diagonal evaluation captured in a CUDA graph:
+    replays equal direct evaluations, including after L changes in place."""
+    sizes = [2, 3, 2]
+    ws = [workload(n, 4, 6.6, 8.0, seed=1000 + k)[0] for k, n in enumerate(sizes)]
+    off = [0]
+    for w in ws:
+        off.append(off[-1] + w["pos"].shape[0])
+    sysb = System(ctx, 4, PREC[dtype], np.concatenate([w["pos"] for w in ws]), [w["cell"] for w in ws],
+                  6.6, 8.0, seg_off=off)
+    cat = {k: to_dev(np.concatenate([w[k] for w in ws]), dtype, ctx.device) for k in ("S", "H", "L")}
+    sysb.autotune(cat["S"], cat["H"], cat["L"], reps=1)
+    graph, out_g, G_g = sysb.capture(cat["S"], cat["H"], cat["L"])
+    for scale in (1.0, 0.9):
+        cat["L"].mul_(scale)
+        graph.replay()
+        torch.cuda.synchronize()
+        out_d, G_d = sysb.energy_grad(cat["S"], cat["H"], cat["L"])
+        assert torch.equal(out_g, out_d) and torch.equal(G_g, G_d)
+    for k, w in enumerate(ws):
+        Lk = w["L"] * 0.9
+        ref = oracle.lnv_energy_grad(w["pos"], w["cell"], 6.6, 8.0,
+                                     rounded(oracle.csr(w["sh_row_ptr"], w["sh_col"], w["S"]), dtype),
+                                     rounded(oracle.csr(w["sh_row_ptr"], w["sh_col"], w["H"]), dtype),
+                                     rounded(oracle.csr(w["l_row_ptr"], w["l_col"], Lk), dtype), grad=False)
+        o = out_g[k].cpu().numpy()
+        tol = TOL[dtype][1]
+        assert abs(o[0] - ref["E"]) <= tol * abs(ref["E"]) * 4
+        assert abs(o[1] - ref["Ne"]) <= tol * abs(ref["Ne"]) * 4
