@@ -6,7 +6,7 @@
 //   Z = L T  masked to R_X      pull product
 //   Tr[XY], Tr[ZY], Tr[XX], Tr[ZX] -> E, N_e   (one fused FP64 trace pass)
 //   Q = H Z  masked to R_L      pull product
-//   W = X^T U^T masked to R_L   pull product (= SL HLS = SLHLS)
+//   W = X^T U^T masked to R_L   (= SL HLS = SLHLS, symmetric: upper triangle only)
 //   G = 6(U + U^T) - 4(Q^T + W + Q) on L's pattern
 // with R_X = R_L + R_SH and R_T = R_L + 2 R_SH: X, Y, T, U are the exact full
 // products (the minimum-image distance obeys the triangle inequality, so A B
@@ -65,6 +65,8 @@ struct lnv_system {
     double r_sh = 0, r_l = 0;
     int64_t *seg_off_dev = nullptr;
     lnv_pattern *P_sh = nullptr, *P_l = nullptr, *P_x = nullptr, *P_t = nullptr;
+    lnv_pattern *P_lu = nullptr;  // upper triangle of P_l: W = SLHLS is symmetric
+    int64_t *w_map = nullptr;     // block of P_l -> its (min, max) block in P_lu
     lnv_plan *pl_xy = nullptr, *pl_tu = nullptr, *pl_z = nullptr, *pl_q = nullptr, *pl_w = nullptr;
     int64_t *sub_lt = nullptr;  // position in P_t of every block of P_l
     void *own_ws = nullptr;
@@ -101,7 +103,7 @@ WsLayout ws_layout(const lnv_system *s, int with_grad)
     L.Z = take(s->P_x->nnzb * bs);
     L.T = take(s->P_t->nnzb * bs);
     L.U = with_grad ? take(s->P_t->nnzb * bs) : 0;
-    L.W = with_grad ? take(s->P_l->nnzb * bs) : 0;
+    L.W = with_grad ? take(s->P_lu->nnzb * bs) : 0;
     L.Q = with_grad ? take(s->P_l->nnzb * bs) : 0;
     L.rows = take(sizeof(double) * 4 * (size_t)std::max<int64_t>(s->n, 1));
     L.total = off;
@@ -113,6 +115,8 @@ void system_free(lnv_system *s)
     if (!s) return;
     plan_free(s->pl_xy); plan_free(s->pl_tu); plan_free(s->pl_z); plan_free(s->pl_q); plan_free(s->pl_w);
     pattern_free(s->P_sh); pattern_free(s->P_l); pattern_free(s->P_x); pattern_free(s->P_t);
+    pattern_free(s->P_lu);
+    cudaFree(s->w_map);
     cudaFree(s->sub_lt);
     cudaFree(s->seg_off_dev);
     cudaFree(s->own_ws);
@@ -342,8 +346,11 @@ lnv_status lnv_system_create(lnv_ctx *ctx, int nsf, lnv_prec prec, const double 
     // the merge-join pull read T's row j in order instead of through tr.
     SYS_TRY(plan_create(ctx, s->P_l, s->P_t, s->P_x, LNV_TRANS_B, &s->pl_z));
     SYS_TRY(plan_create(ctx, s->P_sh, s->P_x, s->P_l, 0, &s->pl_q));
-    SYS_TRY(plan_create(ctx, s->P_x, s->P_t, s->P_l, LNV_TRANS_A | LNV_TRANS_B, &s->pl_w));
+    // W = X^T U^T = SLHLS is symmetric: only its upper triangle is formed
+    SYS_TRY(pattern_upper(ctx, s->P_l, &s->P_lu));
+    SYS_TRY(plan_create(ctx, s->P_x, s->P_t, s->P_lu, LNV_TRANS_A | LNV_TRANS_B, &s->pl_w));
     cudaError_t e = cudaMalloc(&s->sub_lt, sizeof(int64_t) * std::max<int64_t>(s->P_l->nnzb, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&s->w_map, sizeof(int64_t) * std::max<int64_t>(s->P_l->nnzb, 1));
     if (e == cudaSuccess) e = cudaMalloc(&s->seg_off_dev, sizeof(int64_t) * (n_seg + 1));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->seg_off_dev, off.data(), sizeof(int64_t) * (n_seg + 1), cudaMemcpyHostToDevice, ctx->stream);
@@ -353,6 +360,7 @@ lnv_status lnv_system_create(lnv_ctx *ctx, int nsf, lnv_prec prec, const double 
         return e == cudaErrorMemoryAllocation ? LNV_ERR_OOM : LNV_ERR_CUDA;
     }
     SYS_TRY(pattern_submap(ctx, s->P_l, s->P_t, s->sub_lt));
+    SYS_TRY(pattern_upper_map(ctx, s->P_l, s->P_lu, s->w_map));
 #undef SYS_TRY
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
@@ -595,7 +603,7 @@ lnv_status lnv_energy_grad(lnv_ctx *ctx, lnv_system *sys, const void *S_dev, con
         LNV_TRY(multiply(ctx, sys->pl_w, nsf, pr, X, U, W));
         LNV_TRY(mark(6));
         // a7: G = 6(U + U^T) - 4(Q^T + W + Q) on L's pattern
-        LNV_TRY(grad_assemble(ctx, sys->P_l, sys->sub_lt, nsf, pr, U, W, Q, G_dev));
+        LNV_TRY(grad_assemble(ctx, sys->P_l, sys->sub_lt, sys->w_map, nsf, pr, U, W, Q, G_dev));
         LNV_TRY(mark(7));
     }
     return LNV_OK;

@@ -127,6 +127,10 @@ lnv_status pattern_build_impl(lnv_ctx *ctx, const double *pos, int n_seg, const 
 lnv_status pattern_finish(lnv_ctx *ctx, lnv_pattern *p, bool sort_rows);
 lnv_status pattern_validate(lnv_ctx *ctx, const lnv_pattern *p);
 void pattern_free(lnv_pattern *p);
+// Upper triangle (col >= row) of P as its own pattern, and for every block
+// (i, j) of P the position of (min(i,j), max(i,j)) in it.
+lnv_status pattern_upper(lnv_ctx *ctx, const lnv_pattern *P, lnv_pattern **out);
+lnv_status pattern_upper_map(lnv_ctx *ctx, const lnv_pattern *P, const lnv_pattern *U, int64_t *map_dev);
 // position map of every block of `sub` inside `super` (both sorted), -1 if absent
 lnv_status pattern_submap(lnv_ctx *ctx, const lnv_pattern *sub, const lnv_pattern *super,
                           int64_t *map_dev);
@@ -157,7 +161,10 @@ lnv_status trace_rows(lnv_ctx *ctx, const lnv_pattern *P, int nsf, lnv_prec prec
 lnv_status reduce_rows(lnv_ctx *ctx, const double *row_part, int64_t n, int nterms, int n_seg,
                        const int64_t *seg_off_dev, double *out, int stride, int offset);
 lnv_status lnv_combine(lnv_ctx *ctx, int n_seg, double *out);
-lnv_status grad_assemble(lnv_ctx *ctx, const lnv_pattern *PL, const int64_t *sub_LT, int nsf,
-                         lnv_prec prec, const void *U, const void *W, const void *Q, void *G);
+// W is stored on the upper triangle of L's pattern: block (i, j) of L's
+// pattern reads W at w_map[p], transposed when j < i.
+lnv_status grad_assemble(lnv_ctx *ctx, const lnv_pattern *PL, const int64_t *sub_LT,
+                         const int64_t *w_map, int nsf, lnv_prec prec, const void *U, const void *W,
+                         const void *Q, void *G);
 
 }  // namespace lnv

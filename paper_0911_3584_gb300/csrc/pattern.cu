@@ -474,6 +474,61 @@ lnv_status pattern_build_impl(lnv_ctx *ctx, const double *pos, int n_seg, const 
     return LNV_OK;
 }
 
+// Upper triangle (col >= row) of a pattern, as its own (non-symmetric) pattern.
+lnv_status pattern_upper(lnv_ctx *ctx, const lnv_pattern *P, lnv_pattern **out)
+{
+    LNV_TRY(pattern_host_cols(ctx, P));
+    lnv_pattern *u = new lnv_pattern();
+    u->n = P->n;
+    std::vector<int64_t> rp(P->n + 1, 0);
+    std::vector<int32_t> col;
+    col.reserve(P->nnzb / 2 + P->n);
+    for (int64_t i = 0; i < P->n; ++i) {
+        for (int64_t q = P->h_row_ptr[i]; q < P->h_row_ptr[i + 1]; ++q)
+            if (P->h_col[q] >= i) col.push_back(P->h_col[q]);
+        rp[i + 1] = (int64_t)col.size();
+    }
+    cudaError_t e = cudaMalloc(&u->row_ptr, sizeof(int64_t) * (P->n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&u->col, sizeof(int32_t) * std::max<size_t>(col.size(), 1));
+    if (e == cudaSuccess) e = cudaMemcpy(u->row_ptr, rp.data(), sizeof(int64_t) * (P->n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !col.empty())
+        e = cudaMemcpy(u->col, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        pattern_free(u);
+        set_error("upper pattern: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? LNV_ERR_OOM : LNV_ERR_CUDA;
+    }
+    lnv_status s = pattern_finish(ctx, u, false);
+    if (s != LNV_OK) {
+        pattern_free(u);
+        return s;
+    }
+    *out = u;
+    return LNV_OK;
+}
+
+namespace {
+// For every block (i, j) of P: position of (min, max) = (i, j) or (j, i) in U.
+__global__ void k_upper_map(const int32_t *__restrict__ p_row, const int32_t *__restrict__ p_col, int64_t nnzb,
+                            const int64_t *__restrict__ u_rp, const int32_t *__restrict__ u_col, int64_t *map)
+{
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= nnzb) return;
+    const int32_t i = p_row[p], j = p_col[p];
+    const int32_t r = i <= j ? i : j, c = i <= j ? j : i;
+    map[p] = find_col(u_col, u_rp[r], u_rp[r + 1], c);
+}
+}  // namespace
+
+lnv_status pattern_upper_map(lnv_ctx *ctx, const lnv_pattern *P, const lnv_pattern *U, int64_t *map_dev)
+{
+    if (P->nnzb == 0) return LNV_OK;
+    k_upper_map<<<(unsigned)((P->nnzb + 255) / 256), 256, 0, ctx->stream>>>(P->row, P->col, P->nnzb,
+                                                                          U->row_ptr, U->col, map_dev);
+    LNV_LAUNCHED();
+    return LNV_OK;
+}
+
 lnv_status pattern_submap(lnv_ctx *ctx, const lnv_pattern *sub, const lnv_pattern *super,
                           int64_t *map_dev)
 {

@@ -5,11 +5,14 @@
 // tr p the block (j, i) of block p = (i, j).  One warp per row sums its blocks
 // in FP64 (lanes over blocks, then a fixed butterfly), rows are reduced per
 // system by one CTA in a fixed order: the result is run-to-run deterministic.
-// FP32 operands are widened to FP64 before they are multiplied (exactly).
+// The generic kernel widens FP32 operands to FP64 before multiplying
+// (exactly); the fused four-trace kernel forms each block's 16-term dot
+// product in the value precision and sums the blocks in FP64.
 //
 // Gradient: dE/dL = 6(SLH + HLS) - 4(SLSLH + SLHLS + HLSLS) on L's range.
-// With U = SLH (on the R_T pattern), W = SLHLS and Q = HLSLS (on L's
-// pattern), SLH^T = HLS and HLSLS^T = SLSLH (S, H, L symmetric), so
+// With U = SLH (on the R_T pattern), W = SLHLS (symmetric, kept on the upper
+// triangle of L's pattern) and Q = HLSLS (on L's pattern), SLH^T = HLS and
+// HLSLS^T = SLSLH (S, H, L symmetric), so
 //   G_ij = 6 (U_ij + (U_ji)^T) - 4 ((Q_ji)^T + W_ij + Q_ij)
 // is formed in FP64 and stored in the value precision.
 #include "lnv_impl.cuh"
@@ -55,6 +58,83 @@ k_trace_rows(int64_t n, const int64_t *__restrict__ rp, const int64_t *__restric
     }
 }
 
+// The four traces of one evaluation in one pass (NSF = 4): for block p = (i, j)
+// of the R_X pattern and q = (j, i), t1 += <X_p, Y_q^T>, t2 += <Z_p, Y_q^T>,
+// n1 += <X_p, X_q^T>, n2 += <Z_p, X_q^T>; each of X_p, Z_p, X_q, Y_q is loaded
+// once, 16 bytes at a time.  One warp per row, FP64 sums over blocks, fixed
+// butterfly.
+template <typename T>
+__device__ __forceinline__ void ld_blk4(const T *__restrict__ p, T (&b)[16])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 *v = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float4 q = __ldg(v + r);
+            b[4 * r] = q.x; b[4 * r + 1] = q.y; b[4 * r + 2] = q.z; b[4 * r + 3] = q.w;
+        }
+    } else {
+        const double2 *v = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const double2 q = __ldg(v + r);
+            b[2 * r] = q.x; b[2 * r + 1] = q.y;
+        }
+    }
+}
+
+// Each block pair's 16-term dot products are formed in the value precision
+// (T), then accumulated across blocks in FP64: for FP32 values this keeps the
+// trace reduction in FP64 with one conversion per block pair and term.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_trace_lnv4(int64_t n, const int64_t *__restrict__ rp, const int64_t *__restrict__ tr,
+             const T *__restrict__ X, const T *__restrict__ Y, const T *__restrict__ Z,
+             double *__restrict__ row_part)
+{
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    double t1 = 0.0, t2 = 0.0, n1 = 0.0, n2 = 0.0;
+    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+        const int64_t q = __ldg(tr + p);
+        T xp[16], zp[16], xq[16], yq[16];
+        ld_blk4<T>(X + p * 16, xp);
+        ld_blk4<T>(Z + p * 16, zp);
+        ld_blk4<T>(X + q * 16, xq);
+        ld_blk4<T>(Y + q * 16, yq);
+        T a1 = T(0), a2 = T(0), a3 = T(0), a4 = T(0);
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int z = 0; z < 4; ++z) {
+                const T a = xp[x * 4 + z], c = zp[x * 4 + z];
+                const T by = yq[z * 4 + x], bx = xq[z * 4 + x];
+                a1 = fma(a, by, a1);
+                a2 = fma(c, by, a2);
+                a3 = fma(a, bx, a3);
+                a4 = fma(c, bx, a4);
+            }
+        t1 += (double)a1;
+        t2 += (double)a2;
+        n1 += (double)a3;
+        n2 += (double)a4;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+        t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+        n1 += __shfl_xor_sync(0xffffffffu, n1, o);
+        n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    }
+    if (lane == 0) {
+        row_part[i] = t1;
+        row_part[n + i] = t2;
+        row_part[2 * n + i] = n1;
+        row_part[3 * n + i] = n2;
+    }
+}
+
 // out[stride s + offset + t] = sum over the rows of system s of row_part[t][row]
 // (seg_off == nullptr: one system holding every row)
 __global__ void __launch_bounds__(256)
@@ -87,7 +167,8 @@ __global__ void k_combine(int n_seg, double *out)
 
 template <typename T, int NSF>
 __global__ void __launch_bounds__(256)
-k_grad(int64_t nnzb, const int64_t *__restrict__ tr, const int64_t *__restrict__ sub,
+k_grad(int64_t nnzb, const int64_t *__restrict__ tr, const int32_t *__restrict__ row,
+       const int32_t *__restrict__ col, const int64_t *__restrict__ sub, const int64_t *__restrict__ wmap,
        const T *__restrict__ U, const T *__restrict__ W, const T *__restrict__ Q, T *__restrict__ G)
 {
     constexpr int BS = NSF * NSF;
@@ -101,7 +182,10 @@ k_grad(int64_t nnzb, const int64_t *__restrict__ tr, const int64_t *__restrict__
     // missing block would stand for a zero block.
     double u = (u1 >= 0 ? (double)U[u1 * BS + x * NSF + y] : 0.0) +
                (u2 >= 0 ? (double)U[u2 * BS + y * NSF + x] : 0.0);
-    double q = (double)Q[pt * BS + y * NSF + x] + (double)W[p * BS + r] + (double)Q[p * BS + r];
+    // W = SLHLS is symmetric and stored on the upper triangle: W_ij = (W_ji)^T
+    const int64_t wp = wmap[p];
+    const double w = col[p] >= row[p] ? (double)W[wp * BS + r] : (double)W[wp * BS + y * NSF + x];
+    double q = (double)Q[pt * BS + y * NSF + x] + w + (double)Q[p * BS + r];
     G[p * BS + r] = (T)(6.0 * u - 4.0 * q);
 }
 
@@ -140,13 +224,13 @@ lnv_status trace_nsf(lnv_ctx *ctx, const lnv_pattern *P, int nsf, int nterms, co
 }
 
 template <typename T>
-lnv_status grad_nsf(lnv_ctx *ctx, const lnv_pattern *PL, const int64_t *sub, int nsf, const void *U,
-                    const void *W, const void *Q, void *G)
+lnv_status grad_nsf(lnv_ctx *ctx, const lnv_pattern *PL, const int64_t *sub, const int64_t *wmap, int nsf,
+                    const void *U, const void *W, const void *Q, void *G)
 {
     int64_t total = PL->nnzb * (int64_t)nsf * nsf;
     if (total == 0) return LNV_OK;
     unsigned grid = (unsigned)((total + 255) / 256);
-#define GL(N) k_grad<T, N><<<grid, 256, 0, ctx->stream>>>(PL->nnzb, PL->tr, sub, (const T *)U, (const T *)W, (const T *)Q, (T *)G)
+#define GL(N) k_grad<T, N><<<grid, 256, 0, ctx->stream>>>(PL->nnzb, PL->tr, PL->row, PL->col, sub, wmap, (const T *)U, (const T *)W, (const T *)Q, (T *)G)
     switch (nsf) {
     case 1: GL(1); break;
     case 2: GL(2); break;
@@ -167,6 +251,19 @@ lnv_status trace_rows(lnv_ctx *ctx, const lnv_pattern *P, int nsf, lnv_prec prec
     if (!P->symmetric) {
         set_error("trace needs a symmetric pattern");
         return LNV_ERR_PATTERN;
+    }
+    // the LNV four-trace pass {X, Z, X, Z} x {Y, Y, X, X} with 4x4 blocks
+    if (nterms == 4 && nsf == 4 && A[0] == A[2] && A[1] == A[3] && B[0] == B[1] && B[2] == B[3] &&
+        B[2] == A[0] && P->n > 0) {
+        const unsigned grid = (unsigned)((P->n * 32 + 255) / 256);
+        if (prec == LNV_FP64)
+            k_trace_lnv4<double><<<grid, 256, 0, ctx->stream>>>(P->n, P->row_ptr, P->tr, (const double *)A[0],
+                                                                (const double *)B[0], (const double *)A[1], row_part);
+        else
+            k_trace_lnv4<float><<<grid, 256, 0, ctx->stream>>>(P->n, P->row_ptr, P->tr, (const float *)A[0],
+                                                               (const float *)B[0], (const float *)A[1], row_part);
+        LNV_LAUNCHED();
+        return LNV_OK;
     }
     if (prec == LNV_FP64) return trace_nsf<double>(ctx, P, nsf, nterms, A, B, row_part);
     if (prec == LNV_FP32) return trace_nsf<float>(ctx, P, nsf, nterms, A, B, row_part);
@@ -190,11 +287,12 @@ lnv_status lnv_combine(lnv_ctx *ctx, int n_seg, double *out)
     return LNV_OK;
 }
 
-lnv_status grad_assemble(lnv_ctx *ctx, const lnv_pattern *PL, const int64_t *sub_LT, int nsf,
-                         lnv_prec prec, const void *U, const void *W, const void *Q, void *G)
+lnv_status grad_assemble(lnv_ctx *ctx, const lnv_pattern *PL, const int64_t *sub_LT,
+                         const int64_t *w_map, int nsf, lnv_prec prec, const void *U, const void *W,
+                         const void *Q, void *G)
 {
-    if (prec == LNV_FP64) return grad_nsf<double>(ctx, PL, sub_LT, nsf, U, W, Q, G);
-    if (prec == LNV_FP32) return grad_nsf<float>(ctx, PL, sub_LT, nsf, U, W, Q, G);
+    if (prec == LNV_FP64) return grad_nsf<double>(ctx, PL, sub_LT, w_map, nsf, U, W, Q, G);
+    if (prec == LNV_FP32) return grad_nsf<float>(ctx, PL, sub_LT, w_map, nsf, U, W, Q, G);
     set_error("unknown precision %d", (int)prec);
     return LNV_ERR_ARG;
 }
