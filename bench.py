@@ -291,6 +291,20 @@ def w_atoms():
     return 8 * NCELL ** 3
 
 
+def aggregate(total_s: float, atoms_per_rank: int, steps: int, dist=None, device=None):
+    """Whole-job throughput over ranks: every rank times its own `steps`
+    evaluations of `atoms_per_rank` atoms (independent systems, weak scaling);
+    the job time is the slowest rank's.  Returns (atoms/s, max seconds)."""
+    import torch
+    t = torch.tensor([total_s], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    tmax = float(t.item())
+    return atoms_per_rank * world * steps / tmax, tmax
+
+
 def cpu_baseline(w, results):
     """The FP64 CPU oracle on one full evaluation of the same workload."""
     import oracle
@@ -529,11 +543,7 @@ def main():
     e2e32 = e2e(ctx, r32, args.steps, args.warmup)
 
     def agg(res):
-        t = torch.tensor([res["total_s"]], dtype=torch.float64, device=dev)
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = t.item()
-        return w_atoms() * world * args.steps / tmax, tmax
+        return aggregate(res["total_s"], w_atoms(), args.steps, dist, dev)
 
     v32, t32 = agg(r32)
     line = {
