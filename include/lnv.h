@@ -130,8 +130,9 @@ lnv_status lnv_plan_product(lnv_ctx *ctx, const lnv_pattern *A, const lnv_patter
  * binary search of B's row k per output, 2 pull walking B's row j
  * (merge-join; needs a symmetric B pattern), 3 row groups of 4 atoms with a
  * 16-bit position table of op(B), 4 row groups with per-column hit lists,
- * 5 row groups with the table and a cp.async shared-memory pipeline (NSF = 4;
- * other NSF run kernel 3), 6 row groups on tensor cores (mma.sync TF32 with
+ * 5 row groups with the table, per-warp lists of the k's its columns hit and
+ * a cp.async shared-memory ring of op(B) blocks (FP32 values, NSF = 4; other
+ * cases run kernel 3), 6 row groups on tensor cores (mma.sync TF32 with
  * a hi/lo split of both operands, FP32 accumulation; FP32 values, NSF = 4;
  * other cases run kernel 3).
  * The default is 3 when at least half of the table's candidates hit, else 4,

@@ -14,6 +14,7 @@
 #include <atomic>
 #include <cmath>
 #include <map>
+#include <set>
 #include <mutex>
 #include <utility>
 #include <cstdarg>
@@ -42,6 +43,21 @@ cudaError_t ensure_smem(const void *kernel, size_t bytes)
     if (it != set.end() && it->second >= bytes) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) set[key] = bytes;
+    return e;
+}
+
+cudaError_t prefer_smem(const void *kernel)
+{
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;  // (kernel, device)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const std::pair<const void *, int> key(kernel, dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(key)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) done.insert(key);
     return e;
 }
 
@@ -464,7 +480,8 @@ lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
         for (int k = 0; k < 7; ++k)
             if (ms_out) ms_out[si * 7 + k] = -1.0;
         for (int k : {0, 2, 3, 4, 5, 6}) {
-            if (k == 5 && sys->nsf != 4) continue;
+            // per-warp ring kernel: FP32 values, NSF = 4 (elsewhere kernel 5 is kernel 3)
+            if (k == 5 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
             // tensor-core kernel: FP32 values, NSF = 4 (3xTF32, FP32-level accuracy)
             if (k == 6 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
             if (plan_set_kernel(ctx, sg.pl, k) != LNV_OK) continue;

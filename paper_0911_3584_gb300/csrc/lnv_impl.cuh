@@ -52,6 +52,9 @@ constexpr int kMaxRow = 16384;
 // Raise a kernel's dynamic shared-memory limit once (not inside every launch,
 // so that launches can be captured in CUDA graphs).
 cudaError_t ensure_smem(const void *kernel, size_t bytes);
+// Ask for the largest shared-memory carveout for a kernel (once per device),
+// so that shared memory does not cap the CTAs resident per SM.
+cudaError_t prefer_smem(const void *kernel);
 
 }  // namespace lnv
 

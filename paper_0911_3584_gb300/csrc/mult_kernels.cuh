@@ -425,6 +425,13 @@ k_pull2(const int2 *__restrict__ items, const int64_t *__restrict__ a_rp,
 
 // ------------------------------------------------------------------ row groups
 
+// Group index and column chunk of a row-group CTA.  The column chunk is the
+// fastest grid index, so the CTAs of one group run together and the rows of B
+// its K touches are fetched from DRAM about once; groups beyond 65535 go to
+// grid.z.
+__device__ __forceinline__ int64_t grp_of_block() { return blockIdx.y + (int64_t)blockIdx.z * gridDim.y; }
+
+
 // Row-group product (plan built by group.cu).  CTA = (group g of G rows, a
 // chunk of the group's output columns J).  Lanes form groups of NSF, one per
 // output column j; lane r keeps column r of C_(m,j) for the G rows m (and
@@ -629,7 +636,7 @@ k_grp(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
       const int32_t *__restrict__ hp, const int64_t *__restrict__ a_tr,
       const T *__restrict__ a_val, const int64_t *__restrict__ b_rp,
       const T *__restrict__ b_val1, const T *__restrict__ b_val2, T *__restrict__ c_val1,
-      T *__restrict__ c_val2, int jc, int kchunk)
+      T *__restrict__ c_val2, int jc, int kchunk, int64_t n_groups)
 {
     static_assert(NOUT == 1 || NOUT == 2, "one or two products");
     static_assert(NSF % CW == 0, "CW divides NSF");
@@ -644,11 +651,12 @@ k_grp(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
     int32_t *kflag = kact + kchunk + 2;                                          // [kchunk]
     uint16_t *ixs = reinterpret_cast<uint16_t *>(kflag + kchunk + 2);            // [kchunk][jc]
 
-    const int64_t g = blockIdx.x;
+    const int64_t g = grp_of_block();
+    if (g >= n_groups) return;
     const int64_t kb = k_off[g], nk = k_off[g + 1] - kb;
     const int64_t jb = j_off[g], nj = j_off[g + 1] - jb;
     const int64_t nj_pad = (nj + 7) & ~int64_t(7);
-    const int64_t j0 = (int64_t)blockIdx.y * jc;
+    const int64_t j0 = (int64_t)blockIdx.x * jc;
     if (j0 >= nj) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int jg = lane / LPJ, c0 = (lane - jg * LPJ) * CW;
@@ -801,7 +809,7 @@ k_grp(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
     }
 }
 
-// ------------------------------------------------------------------ row groups, pipelined
+// ------------------------------------------------------------------ row groups, per-warp k lists
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes)
 {
@@ -816,165 +824,234 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Row-group product with a two-stage shared-memory pipeline (NSF = 4).  CTA =
-// (group g, JC = 64 output columns).  Per k-chunk of KC k's the CTA gathers
-// op(B)_kj for every (k, j) of the chunk x its columns into shared memory
-// with 16-byte cp.async copies (zero-filled where the dense position table
-// has no block), plus A's blocks of the G rows; while chunk c is multiplied
-// out of shared memory, chunk c+1's copies are in flight.  Four lanes share
-// an output column j (lane r keeps column r of C_(m,j) for every row m) and
-// each lane group owns two columns.  op(B) = B^T makes row r of the stored
-// block column r of op(B); otherwise the block is stored transposed in shared
-// memory so the same 16-byte read serves.  Sums run over k in ascending order.
-template <typename T, int G, int KC, bool TA, bool TB>
-__global__ void __launch_bounds__(128)
-k_gpipe(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
-        const int32_t *__restrict__ apos, const int64_t *__restrict__ j_off,
-        const int32_t *__restrict__ j_list, const int32_t *__restrict__ cpos,
-        const int64_t *__restrict__ bidx_off, const uint16_t *__restrict__ bidx,
-        const int64_t *__restrict__ a_tr, const T *__restrict__ a_val,
-        const int64_t *__restrict__ b_rp, const T *__restrict__ b_val, T *__restrict__ c_val)
-{
-    constexpr int NSF = 4, BS = 16, JC = 64, CPB = BS * sizeof(T) / 16;  // 16-byte chunks per block
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *Bt = reinterpret_cast<T *>(smem_raw);                 // [2][KC][JC][BS]
-    T *At = Bt + 2 * KC * JC * BS;                           // [2][KC][G][BS]
-    uint32_t *msk = reinterpret_cast<uint32_t *>(At + 2 * KC * G * BS);  // [2][KC]
 
-    const int64_t g = blockIdx.x;
+// Row-group product with per-warp k lists and a cp.async ring (FP32, NSF = 4,
+// G = 4 rows, 4 warps, 64 output columns per CTA).  Warp w owns the 16
+// consecutive columns [16w, 16w + 16) of the CTA's chunk of the group's J, as
+// two sets of eight (o = 0, 1); in each set four lanes share a column j and
+// lane r keeps column r of C_(m,j) for the G rows m and NOUT products.
+// Per k-chunk the CTA stages A's blocks of the G rows (op(A), row-major, zero
+// where absent, 16-byte stores), a bitmask of the rows holding A_mk and the
+// position-table tile of its columns.  Each warp then lists the k's at which
+// any of its 16 columns has a block (with a 2-bit mask of the sets that do),
+// so it neither loads nor multiplies at k's that miss all its columns.  Lanes
+// copy row r of op(B)_kj's stored block (16 bytes, zero-filled at a miss)
+// into a warp-private ring of D stages with cp.async, D - 1 list entries
+// ahead of the one being multiplied.  Stored block rows are columns of op(B)
+// when op(B) = B^T; otherwise the four lanes of a column read column r across
+// the rows their group copied (slots padded to 80 bytes, conflict-free).
+// Sums run over k in ascending order (deterministic).
+template <int NOUT, int D, bool TA, bool TB>
+__global__ void __launch_bounds__(128, 4)
+k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
+     const int32_t *__restrict__ apos, const int64_t *__restrict__ j_off,
+     const int32_t *__restrict__ j_list, const int32_t *__restrict__ cpos,
+     const int64_t *__restrict__ bidx_off, const uint16_t *__restrict__ bidx,
+     const int64_t *__restrict__ a_tr, const float *__restrict__ a_val,
+     const int64_t *__restrict__ b_rp, const float *__restrict__ b_val1,
+     const float *__restrict__ b_val2, float *__restrict__ c_val1, float *__restrict__ c_val2,
+     int kchunk, int64_t n_groups)
+{
+    static_assert(NOUT == 1 || NOUT == 2, "one or two products");
+    constexpr int G = 4, BS = 16, NW = 4, JPW = 8, OPT = 2, JC = NW * JPW * OPT;
+    constexpr int SLOT = TB ? 16 : 20;                  // floats per block slot in the ring
+    constexpr int STAGE = OPT * NOUT * JPW * SLOT;      // floats per warp and stage
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *ring = reinterpret_cast<float *>(smem_raw);                                   // [NW][D][STAGE]
+    float *a_s = ring + NW * D * STAGE;                                                  // [kchunk][G][BS]
+    int64_t *brow = reinterpret_cast<int64_t *>(a_s + (size_t)kchunk * G * BS);          // [kchunk]
+    uint16_t *ixs = reinterpret_cast<uint16_t *>(brow + kchunk);                         // [kchunk][JC]
+    uint32_t *msk = reinterpret_cast<uint32_t *>(ixs + (size_t)kchunk * JC);             // [kchunk]
+    int32_t *wl = reinterpret_cast<int32_t *>(msk + kchunk);                             // [NW][kchunk]
+
+    const int64_t g = grp_of_block();
+    if (g >= n_groups) return;
     const int64_t kb = k_off[g], nk = k_off[g + 1] - kb;
     const int64_t jb = j_off[g], nj = j_off[g + 1] - jb;
-    const int64_t j0 = (int64_t)blockIdx.y * JC;
+    const int64_t nj_pad = (nj + 7) & ~int64_t(7);
+    const int64_t j0 = (int64_t)blockIdx.x * JC;
     if (j0 >= nj) return;
     const int jcn = (int)min((int64_t)JC, nj - j0);
-    const uint16_t *bx = bidx + bidx_off[g];
-    const int tid = threadIdx.x;
-    const int lg = tid >> 2, r = tid & 3;  // lane group 0..31 owns columns lg and lg + 32
-    const int64_t nchunks = (nk + KC - 1) / KC;
-
-    // issue the copies of chunk c into buffer c & 1
-    auto issue = [&](int64_t c) {
-        const int buf = (int)(c & 1);
-        const int64_t k0 = c * KC;
-        const int kn = (int)min((int64_t)KC, nk - k0);
-        T *bt = Bt + buf * KC * JC * BS;
-        // op(B) blocks: KC x JC blocks of CPB 16-byte chunks
-        for (int t = tid; t < KC * JC * CPB; t += 128) {
-            const int blk = t / CPB, ch = t - blk * CPB;
-            const int kk = blk / JC, jj = blk - kk * JC;
-            const T *src = b_val;
-            int bytes = 0;
-            if (kk < kn && jj < jcn) {
-                const uint16_t ix = __ldg(bx + (k0 + kk) * ((nj + 7) & ~int64_t(7)) + j0 + jj);
-                if (ix != 0xFFFF) {
-                    const int64_t row = TB ? b_rp[j_list[jb + j0 + jj]] : b_rp[k_list[kb + k0 + kk]];
-                    src = b_val + (row + ix) * BS + ch * (16 / sizeof(T));
-                    bytes = 16;
-                }
-            }
-            if (TB) {
-                cp_async16(bt + (size_t)blk * BS + ch * (16 / sizeof(T)), src, bytes);
-            } else {
-                // stored block (k, j) row-major; op(B)[z][y] = blk[z][y].  Keep it as is:
-                // the consumer reads column r of op(B) from rows z (see below).
-                cp_async16(bt + (size_t)blk * BS + ch * (16 / sizeof(T)), src, bytes);
-            }
-        }
-        // A blocks of the G rows (transposed in registers when TA)
-        T *at = At + buf * KC * G * BS;
-        for (int t = tid; t < KC * G * BS; t += 128) {
-            const int kk = t / (G * BS), rem = t - kk * (G * BS), m = rem / BS, e = rem - m * BS;
-            T v = T(0);
-            if (kk < kn) {
-                const int32_t q = apos[(kb + k0 + kk) * G + m];
-                if (q >= 0) {
-                    if (TA) {
-                        const int x = e / NSF, z = e % NSF;
-                        v = a_val[a_tr[q] * BS + z * NSF + x];
-                    } else {
-                        v = a_val[(int64_t)q * BS + e];
-                    }
-                }
-            }
-            at[t] = v;
-        }
-        for (int t = tid; t < KC; t += 128) {
-            uint32_t mm = 0;
-            if (t < kn)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int jg = lane >> 2, r = lane & 3;
+    int col[OPT];
+    bool jv[OPT];
+    int64_t brj[OPT];
 #pragma unroll
-                for (int m = 0; m < G; ++m) mm |= (apos[(kb + k0 + t) * G + m] >= 0 ? 1u : 0u) << m;
-            msk[buf * KC + t] = mm;
-        }
-        cp_async_commit();
-    };
+    for (int o = 0; o < OPT; ++o) {
+        col[o] = warp * (JPW * OPT) + o * JPW + jg;
+        jv[o] = col[o] < jcn;
+        brj[o] = (TB && jv[o]) ? b_rp[j_list[jb + j0 + col[o]]] : 0;
+    }
+    const bool warp_live = warp * (JPW * OPT) < jcn;
+    float *wring = ring + warp * D * STAGE;
+    int32_t *wlist = wl + warp * kchunk;
 
-    T acc[2][G][NSF];
+    float acc[OPT][G][NOUT][4];
 #pragma unroll
-    for (int o = 0; o < 2; ++o)
+    for (int o = 0; o < OPT; ++o)
 #pragma unroll
         for (int m = 0; m < G; ++m)
 #pragma unroll
-            for (int x = 0; x < NSF; ++x) acc[o][m][x] = T(0);
+            for (int n = 0; n < NOUT; ++n)
+#pragma unroll
+                for (int x = 0; x < 4; ++x) acc[o][m][n][x] = 0.f;
 
-    issue(0);
-    for (int64_t c = 0; c < nchunks; ++c) {
-        if (c + 1 < nchunks) {
-            issue(c + 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+    for (int64_t k0 = 0; k0 < nk; k0 += kchunk) {
+        const int kn = (int)min((int64_t)kchunk, nk - k0);
+        __syncthreads();
+        // A's blocks: one thread per (k, row m, block row x), 16-byte stores
+        for (int t = tid; t < kn * G * 4; t += 128) {
+            const int x = t & 3, km = t >> 2;
+            const int kk = km / G, m = km - kk * G;
+            const int32_t q = __ldg(apos + (kb + k0 + kk) * G + m);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q >= 0) {
+                if (TA) {
+                    // row x of op(A) = column x of the stored block
+                    const float *p = a_val + __ldg(a_tr + q) * BS;
+                    v = make_float4(__ldg(p + x), __ldg(p + 4 + x), __ldg(p + 8 + x), __ldg(p + 12 + x));
+                } else {
+                    v = __ldg(reinterpret_cast<const float4 *>(a_val + (int64_t)q * BS) + x);
+                }
+            }
+            *reinterpret_cast<float4 *>(a_s + (size_t)km * BS + x * 4) = v;
+        }
+        for (int t = tid; t < kn; t += 128) {
+            uint32_t mm = 0;
+#pragma unroll
+            for (int m = 0; m < G; ++m) mm |= (__ldg(apos + (kb + k0 + t) * G + m) >= 0 ? 1u : 0u) << m;
+            msk[t] = mm;
+            brow[t] = TB ? 0 : b_rp[k_list[kb + k0 + t]];
+        }
+        // position-table tile [kn][JC], 16 bytes at a time, 0xFFFF past the group's columns
+        {
+            const uint16_t *bx = bidx + bidx_off[g];
+            for (int t = tid; t < kn * (JC / 8); t += 128) {
+                const int kk = t / (JC / 8), c = (t - kk * (JC / 8)) * 8;
+                uint4 w = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+                if (c < jcn) {
+                    w = __ldg(reinterpret_cast<const uint4 *>(bx + (k0 + kk) * nj_pad + j0 + c));
+                    if (c + 8 > jcn) {
+                        uint16_t e[8];
+                        memcpy(e, &w, 16);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            if (c + u >= jcn) e[u] = 0xFFFF;
+                        memcpy(&w, e, 16);
+                    }
+                }
+                *reinterpret_cast<uint4 *>(ixs + (size_t)kk * JC + c) = w;
+            }
         }
         __syncthreads();
-        const int buf = (int)(c & 1);
-        const T *bt = Bt + buf * KC * JC * BS;
-        const T *at = At + buf * KC * G * BS;
-        const uint32_t *mk = msk + buf * KC;
-#pragma unroll 2
-        for (int kk = 0; kk < KC; ++kk) {
-            const uint32_t mm = mk[kk];
-            if (mm == 0) continue;  // past the end of K
-            T v[2][NSF];
+        if (!warp_live) continue;
+
+        // this warp's k list: entry = kk | (set mask << 16)
+        int na = 0;
+        for (int kq = 0; kq < kn; kq += 32) {
+            const int kk = kq + lane;
+            uint32_t om = 0;
+            if (kk < kn) {
+                const uint4 *row = reinterpret_cast<const uint4 *>(ixs + (size_t)kk * JC + warp * (JPW * OPT));
+                const uint4 v0 = row[0], v1 = row[1];
+                om = ((v0.x & v0.y & v0.z & v0.w) != 0xFFFFFFFFu ? 1u : 0u) |
+                     ((v1.x & v1.y & v1.z & v1.w) != 0xFFFFFFFFu ? 2u : 0u);
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, om != 0);
+            if (om) wlist[na + __popc(b & ((1u << lane) - 1u))] = kk | (int)(om << 16);
+            na += __popc(b);
+        }
+        __syncwarp();
+
+        // copy list entry q into ring stage s (an empty commit group past the end)
+        auto issue = [&](int q) {
+            if (q < na) {
+                const int e = wlist[q], kk = e & 0xFFFF, om = e >> 16;
+                float *st = wring + (q % D) * STAGE;
 #pragma unroll
-            for (int o = 0; o < 2; ++o) {
-                const T *blk = bt + (size_t)(kk * JC + lg + 32 * o) * BS;
-                // v[o][z] = op(B)_kj[z][r]
-                if (TB) ld_row<T, NSF>(blk + r * NSF, v[o], false);
-                else {
+                for (int o = 0; o < OPT; ++o) {
+                    if (!((om >> o) & 1)) continue;
+                    const uint16_t ix = jv[o] ? ixs[(size_t)kk * JC + col[o]] : (uint16_t)0xFFFF;
+                    const bool hit = ix != 0xFFFF;
+                    const int64_t p = ((TB ? brj[o] : brow[kk]) + ix) * BS + r * 4;
 #pragma unroll
-                    for (int z = 0; z < NSF; ++z) v[o][z] = blk[z * NSF + r];
+                    for (int n = 0; n < NOUT; ++n) {
+                        const float *bv = n == 0 ? b_val1 : b_val2;
+                        cp_async16(st + ((o * NOUT + n) * JPW + jg) * SLOT + r * 4, hit ? bv + p : bv,
+                                   hit ? 16 : 0);
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int q = 0; q < D - 1; ++q) issue(q);
+        for (int q = 0; q < na; ++q) {
+            issue(q + D - 1);
+            cp_async_wait<D - 1>();
+            __syncwarp();
+            const int e = wlist[q], kk = e & 0xFFFF, om = e >> 16;
+            const float *st = wring + (q % D) * STAGE;
+            const uint32_t mk = msk[kk];
+            // op(B)_kj column r of each (set, product): bv[o][n][z] = op(B)[z][r]
+            float bv[OPT][NOUT][4];
+#pragma unroll
+            for (int o = 0; o < OPT; ++o) {
+#pragma unroll
+                for (int n = 0; n < NOUT; ++n) {
+                    const float *blk = st + ((o * NOUT + n) * JPW + jg) * SLOT;
+                    if (!((om >> o) & 1)) {
+#pragma unroll
+                        for (int z = 0; z < 4; ++z) bv[o][n][z] = 0.f;
+                    } else if (TB) {
+                        const float4 v = *reinterpret_cast<const float4 *>(blk + r * 4);
+                        bv[o][n][0] = v.x; bv[o][n][1] = v.y; bv[o][n][2] = v.z; bv[o][n][3] = v.w;
+                    } else {
+#pragma unroll
+                        for (int z = 0; z < 4; ++z) bv[o][n][z] = blk[z * 4 + r];
+                    }
                 }
             }
 #pragma unroll
             for (int m = 0; m < G; ++m) {
-                if (!((mm >> m) & 1u)) continue;
-                const T *am = at + (kk * G + m) * BS;
+                if (!((mk >> m) & 1u)) continue;
+                const float4 *am = reinterpret_cast<const float4 *>(a_s + ((size_t)kk * G + m) * BS);
+                float a[4][4];
 #pragma unroll
-                for (int x = 0; x < NSF; ++x) {
-                    T a[NSF];
-                    ld_row<T, NSF>(am + x * NSF, a, false);
+                for (int x = 0; x < 4; ++x) {
+                    const float4 v = am[x];
+                    a[x][0] = v.x; a[x][1] = v.y; a[x][2] = v.z; a[x][3] = v.w;
+                }
 #pragma unroll
-                    for (int o = 0; o < 2; ++o) {
-                        T s = acc[o][m][x];
+                for (int o = 0; o < OPT; ++o) {
+                    if (!((om >> o) & 1)) continue;
 #pragma unroll
-                        for (int z = 0; z < NSF; ++z) s = fma(a[z], v[o][z], s);
-                        acc[o][m][x] = s;
-                    }
+                    for (int z = 0; z < 4; ++z)
+#pragma unroll
+                        for (int n = 0; n < NOUT; ++n)
+#pragma unroll
+                            for (int x = 0; x < 4; ++x)
+                                acc[o][m][n][x] = fmaf(a[x][z], bv[o][n][z], acc[o][m][n][x]);
                 }
             }
+            __syncwarp();
         }
-        __syncthreads();
+        cp_async_wait<0>();
     }
 #pragma unroll
-    for (int o = 0; o < 2; ++o) {
-        const int jj = lg + 32 * o;
-        if (jj >= jcn) continue;
+    for (int o = 0; o < OPT; ++o) {
+        if (!jv[o]) continue;
 #pragma unroll
         for (int m = 0; m < G; ++m) {
-            const int32_t pos = cpos[(jb + j0 + jj) * G + m];
+            const int32_t pos = cpos[(jb + j0 + col[o]) * G + m];
             if (pos < 0) continue;
-            T *dst = c_val + (int64_t)pos * BS;
 #pragma unroll
-            for (int x = 0; x < NSF; ++x) dst[x * NSF + r] = acc[o][m][x];
+            for (int n = 0; n < NOUT; ++n) {
+                float *dst = (n == 0 ? c_val1 : c_val2) + (int64_t)pos * BS;
+#pragma unroll
+                for (int x = 0; x < 4; ++x) dst[x * 4 + r] = acc[o][m][n][x];
+            }
         }
     }
 }
@@ -1017,7 +1094,7 @@ k_gmma(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
        const int64_t *__restrict__ a_tr, const float *__restrict__ a_val,
        const int64_t *__restrict__ b_rp, const float *__restrict__ b_val1,
        const float *__restrict__ b_val2, float *__restrict__ c_val1, float *__restrict__ c_val2,
-       int kchunk)
+       int kchunk, int64_t n_groups)
 {
     constexpr int G = 4, NSF = 4, BS = 16;
     constexpr int JC = 4 * NT * 2;  // output columns per CTA
@@ -1029,11 +1106,12 @@ k_gmma(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
     int32_t *kflag = kact + kchunk + 2;                                          // [kchunk + 2]
     uint16_t *ixs = reinterpret_cast<uint16_t *>(kflag + kchunk + 2);            // [kchunk][JC]
 
-    const int64_t g = blockIdx.x;
+    const int64_t g = grp_of_block();
+    if (g >= n_groups) return;
     const int64_t kb = k_off[g], nk = k_off[g + 1] - kb;
     const int64_t jb = j_off[g], nj = j_off[g + 1] - jb;
     const int64_t nj_pad = (nj + 7) & ~int64_t(7);
-    const int64_t j0 = (int64_t)blockIdx.y * JC;
+    const int64_t j0 = (int64_t)blockIdx.x * JC;
     if (j0 >= nj) return;
     const int jcn = (int)min((int64_t)JC, nj - j0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1199,6 +1277,13 @@ constexpr int group_cw()
     return NSF == 9 ? 3 : (NSF == 4 ? 1 : NSF);
 }
 
+// Grid of a row-group launch: (column chunks, groups), groups past 65535 in z.
+inline dim3 group_grid(int64_t n_groups, int64_t max_j, int jc)
+{
+    const int64_t gy = std::min<int64_t>(n_groups, 65535);
+    return dim3((unsigned)((max_j + jc - 1) / jc), (unsigned)gy, (unsigned)((n_groups + gy - 1) / gy));
+}
+
 template <typename T, int NSF, int G, int NOUT, bool TA, bool TB, bool SPARSE>
 lnv_status launch_grp(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
                       const void *B2, void *C1, void *C2)
@@ -1221,29 +1306,43 @@ lnv_status launch_grp(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const voi
     const size_t smem = (size_t)kchunk * per_k + 128;
     auto kern = k_grp<T, NSF, G, NOUT, CW, OPT, TA, TB, SPARSE>;
     LNV_CUDA(ensure_smem((const void *)kern, smem));
-    dim3 grid((unsigned)gp.n_groups, (unsigned)((gp.max_j + jc - 1) / jc));
-    kern<<<grid, kGroupThreads, smem, ctx->stream>>>(
+    LNV_CUDA(prefer_smem((const void *)kern));
+    kern<<<group_grid(gp.n_groups, gp.max_j, jc), kGroupThreads, smem, ctx->stream>>>(
         gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list, gp.cpos, gp.bidx_off, gp.bidx, gp.hoff,
         gp.hk, gp.hp, pl->A->tr, (const T *)A, pl->B->row_ptr, (const T *)B1, (const T *)B2,
-        (T *)C1, (T *)C2, jc, kchunk);
+        (T *)C1, (T *)C2, jc, kchunk, gp.n_groups);
     LNV_LAUNCHED();
     return LNV_OK;
 }
 
-template <typename T, bool TA, bool TB>
-lnv_status launch_gpipe(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B, void *C)
+template <int NOUT, bool TA, bool TB>
+lnv_status launch_gw(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1, const void *B2,
+                     void *C1, void *C2)
 {
-    constexpr int G = 4, BS = 16, JC = 64;
-    constexpr int KC = sizeof(T) == 4 ? 8 : 4;
+    constexpr int G = 4, BS = 16, NW = 4, JC = 64, D = 3;
+    constexpr int SLOT = TB ? 16 : 20;
+    constexpr size_t ring = sizeof(float) * NW * D * 2 * NOUT * 8 * SLOT;
     const GroupPlan &gp = pl->grp;
     if (gp.n_groups == 0 || gp.max_j == 0) return LNV_OK;
-    const size_t smem = sizeof(T) * (2 * KC * JC * BS + 2 * KC * G * BS) + sizeof(uint32_t) * 2 * KC + 64;
-    auto kern = k_gpipe<T, G, KC, TA, TB>;
+    if (!gp.bidx && gp.candidates > 0) {
+        set_error("row-group plan lacks the position table");
+        return LNV_ERR_UNSUPPORTED;
+    }
+    // four CTAs per SM: 228 KB of shared memory, 1 KB of it reserved per CTA
+    const size_t per_k = sizeof(float) * G * BS + sizeof(int64_t) + sizeof(uint16_t) * JC +
+                         sizeof(uint32_t) + sizeof(int32_t) * NW;
+    const size_t room = 228 * 1024 / 4 - 1024 - ring;
+    int kchunk = (int)std::min<size_t>(room / per_k, 65535);
+    kchunk = std::min(kchunk, (int)((std::max(gp.max_k, 1) + 7) & ~7));
+    kchunk &= ~7;  // keeps the position tile 16-byte aligned
+    const size_t smem = ring + (size_t)kchunk * per_k;
+    auto kern = k_gw<NOUT, D, TA, TB>;
     LNV_CUDA(ensure_smem((const void *)kern, smem));
-    dim3 grid((unsigned)gp.n_groups, (unsigned)((gp.max_j + JC - 1) / JC));
-    kern<<<grid, 128, smem, ctx->stream>>>(gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list,
-                                          gp.cpos, gp.bidx_off, gp.bidx, pl->A->tr, (const T *)A,
-                                          pl->B->row_ptr, (const T *)B, (T *)C);
+    LNV_CUDA(prefer_smem((const void *)kern));
+    kern<<<group_grid(gp.n_groups, gp.max_j, JC), 128, smem, ctx->stream>>>(
+        gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list, gp.cpos, gp.bidx_off, gp.bidx, pl->A->tr,
+        (const float *)A, pl->B->row_ptr, (const float *)B1, (const float *)B2, (float *)C1, (float *)C2,
+        kchunk, gp.n_groups);
     LNV_LAUNCHED();
     return LNV_OK;
 }
@@ -1265,11 +1364,10 @@ lnv_status launch_gmma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const vo
     const size_t smem = (size_t)kchunk * per_k + 128;
     auto kern = k_gmma<NOUT, NT, TA, TB>;
     LNV_CUDA(ensure_smem((const void *)kern, smem));
-    dim3 grid((unsigned)gp.n_groups, (unsigned)((gp.max_j + JC - 1) / JC));
-    kern<<<grid, 128, smem, ctx->stream>>>(gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list, gp.cpos,
-                                          gp.bidx_off, gp.bidx, pl->A->tr, (const float *)A,
-                                          pl->B->row_ptr, (const float *)B1, (const float *)B2,
-                                          (float *)C1, (float *)C2, kchunk);
+    kern<<<group_grid(gp.n_groups, gp.max_j, JC), 128, smem, ctx->stream>>>(
+        gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list, gp.cpos, gp.bidx_off, gp.bidx, pl->A->tr,
+        (const float *)A, pl->B->row_ptr, (const float *)B1, (const float *)B2, (float *)C1, (float *)C2,
+        kchunk, gp.n_groups);
     LNV_LAUNCHED();
     return LNV_OK;
 }
@@ -1281,11 +1379,10 @@ lnv_status launch_group(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const v
     if constexpr (NSF == 4 && sizeof(T) == 4) {
         if (pl->mode == 6) return launch_gmma<NOUT, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
     }
-    if constexpr (NSF == 4) {
+    if constexpr (NSF == 4 && sizeof(T) == 4) {
         if (pl->mode == 5) {
-            LNV_TRY((launch_gpipe<T, TA, TB>(ctx, pl, A, B1, C1)));
-            if (B2) LNV_TRY((launch_gpipe<T, TA, TB>(ctx, pl, A, B2, C2)));
-            return LNV_OK;
+            if (B2) return launch_gw<2, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
+            return launch_gw<1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr);
         }
     }
     if (pl->grp.G != 4) {
