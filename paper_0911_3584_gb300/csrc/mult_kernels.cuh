@@ -825,67 +825,76 @@ __device__ __forceinline__ void cp_async_wait()
 }
 
 
-// Row-group product with per-warp k lists and a cp.async ring (FP32, NSF = 4,
-// G = 4 rows, 4 warps, 64 output columns per CTA).  Warp w owns the 16
-// consecutive columns [16w, 16w + 16) of the CTA's chunk of the group's J, as
-// two sets of eight (o = 0, 1); in each set four lanes share a column j and
-// lane r keeps column r of C_(m,j) for the G rows m and NOUT products.
-// Per k-chunk the CTA stages A's blocks of the G rows (op(A), row-major, zero
-// where absent, 16-byte stores), a bitmask of the rows holding A_mk and the
-// position-table tile of its columns.  Each warp then lists the k's at which
-// any of its 16 columns has a block (with a 2-bit mask of the sets that do),
-// so it neither loads nor multiplies at k's that miss all its columns.  Lanes
-// copy row r of op(B)_kj's stored block (16 bytes, zero-filled at a miss)
-// into a warp-private ring of D stages with cp.async, D - 1 list entries
-// ahead of the one being multiplied.  Stored block rows are columns of op(B)
-// when op(B) = B^T; otherwise the four lanes of a column read column r across
-// the rows their group copied (slots padded to 80 bytes, conflict-free).
-// Sums run over k in ascending order (deterministic).
+// Row-group product with independent warps (FP32, NSF = 4, G = 4 rows).
+//
+// A warp owns one slice of the group's output columns J: OPT sets of eight
+// consecutive columns (OPT = 2 for two fused products, 4 for one).  In a set,
+// four lanes share a column j and lane r keeps column r of C_(m,j) for the G
+// rows m and NOUT products in registers.  Warps share nothing, so there is no
+// block-wide barrier: per chunk of KC k's of the group's K, the warp lists
+// the k's at which any of its columns holds op(B)_kj (one lane per k, ballot
+// compaction).  An entry carries k, a bitmask of the sets that hit, a bitmask
+// of the rows m holding A_mk, A's block positions and the 16-bit positions of
+// op(B)_kj for the warp's columns.  For each entry the warp copies A's blocks
+// (rows with A_mk only) and the stored rows of op(B)_kj (16 bytes per lane,
+// zero-filled at a miss) into a warp-private ring of D stages with cp.async,
+// D - 1 entries ahead of the one being multiplied.  Stored block rows are
+// columns of op(B) when op(B) = B^T, else lanes read column r across the four
+// rows of the block; the four rows of a block slot are rotated by (jg / 2) so
+// those column reads are free of bank conflicts.  A is read the same way:
+// rows of op(A), or of the stored block when op(A) = A^T.  Sums run over k in
+// ascending order (deterministic).  Outputs (m, j) outside C's pattern are
+// discarded at the store.
 template <int NOUT, int D, bool TA, bool TB>
-__global__ void __launch_bounds__(128, 4)
-k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
-     const int32_t *__restrict__ apos, const int64_t *__restrict__ j_off,
-     const int32_t *__restrict__ j_list, const int32_t *__restrict__ cpos,
-     const int64_t *__restrict__ bidx_off, const uint16_t *__restrict__ bidx,
+struct GwShape {
+    static constexpr int G = 4, BS = 16, OPT = NOUT == 2 ? 2 : 4, COLS = 8 * OPT;
+    static constexpr int KC = NOUT == 2 ? 64 : 48;                 // k's per list chunk
+    // list entry: k | set mask << 16 | row mask << 24, A's four block positions,
+    // the row start of op(B)'s k when op(B) = B, a pad word, then the 16-bit
+    // positions of op(B)_kj for the warp's columns (odd size: no bank conflicts)
+    static constexpr int EW = 7 + COLS / 2;
+    static constexpr int STAGE = G * BS + OPT * NOUT * 8 * BS;     // floats per ring stage
+    static constexpr size_t warp_bytes = sizeof(float) * D * STAGE + sizeof(int32_t) * KC * EW;
+};
+
+template <int NOUT, int D, int NW, bool TA, bool TB>
+__global__ void __launch_bounds__(NW * 32, 16 / NW)
+k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
+     const int64_t *__restrict__ j_off, const int32_t *__restrict__ j_list,
+     const int32_t *__restrict__ cpos, const int64_t *__restrict__ bidx_off,
+     const uint16_t *__restrict__ bidx, const int32_t *__restrict__ k_list,
      const int64_t *__restrict__ a_tr, const float *__restrict__ a_val,
      const int64_t *__restrict__ b_rp, const float *__restrict__ b_val1,
      const float *__restrict__ b_val2, float *__restrict__ c_val1, float *__restrict__ c_val2,
-     int kchunk, int64_t n_groups)
+     int64_t n_groups)
 {
-    static_assert(NOUT == 1 || NOUT == 2, "one or two products");
-    constexpr int G = 4, BS = 16, NW = 4, JPW = 8, OPT = 2, JC = NW * JPW * OPT;
-    constexpr int SLOT = TB ? 16 : 20;                  // floats per block slot in the ring
-    constexpr int STAGE = OPT * NOUT * JPW * SLOT;      // floats per warp and stage
+    using S = GwShape<NOUT, D, TA, TB>;
+    constexpr int G = S::G, BS = S::BS, OPT = S::OPT, COLS = S::COLS, KC = S::KC, EW = S::EW;
+    constexpr int STAGE = S::STAGE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *ring = reinterpret_cast<float *>(smem_raw);                                   // [NW][D][STAGE]
-    float *a_s = ring + NW * D * STAGE;                                                  // [kchunk][G][BS]
-    int64_t *brow = reinterpret_cast<int64_t *>(a_s + (size_t)kchunk * G * BS);          // [kchunk]
-    uint16_t *ixs = reinterpret_cast<uint16_t *>(brow + kchunk);                         // [kchunk][JC]
-    uint32_t *msk = reinterpret_cast<uint32_t *>(ixs + (size_t)kchunk * JC);             // [kchunk]
-    int32_t *wl = reinterpret_cast<int32_t *>(msk + kchunk);                             // [NW][kchunk]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *ring = reinterpret_cast<float *>(smem_raw) + (size_t)warp * D * STAGE;                 // [D][STAGE]
+    int32_t *list = reinterpret_cast<int32_t *>(reinterpret_cast<float *>(smem_raw) + (size_t)NW * D * STAGE) +
+                    (size_t)warp * KC * EW;                                                       // [KC][EW]
 
     const int64_t g = grp_of_block();
     if (g >= n_groups) return;
     const int64_t kb = k_off[g], nk = k_off[g + 1] - kb;
     const int64_t jb = j_off[g], nj = j_off[g + 1] - jb;
     const int64_t nj_pad = (nj + 7) & ~int64_t(7);
-    const int64_t j0 = (int64_t)blockIdx.x * JC;
+    const int64_t j0 = ((int64_t)blockIdx.x * NW + warp) * COLS;
     if (j0 >= nj) return;
-    const int jcn = (int)min((int64_t)JC, nj - j0);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int jcn = (int)min((int64_t)COLS, nj - j0);
     const int jg = lane >> 2, r = lane & 3;
-    int col[OPT];
+    const int prow = (r + (jg >> 1)) & 3;  // rotated slot row of stored row r
+    int32_t brj[OPT];  // row start of op(B)'s column j when op(B) = B^T
     bool jv[OPT];
-    int64_t brj[OPT];
 #pragma unroll
     for (int o = 0; o < OPT; ++o) {
-        col[o] = warp * (JPW * OPT) + o * JPW + jg;
-        jv[o] = col[o] < jcn;
-        brj[o] = (TB && jv[o]) ? b_rp[j_list[jb + j0 + col[o]]] : 0;
+        jv[o] = o * 8 + jg < jcn;
+        brj[o] = (TB && jv[o]) ? (int32_t)b_rp[j_list[jb + j0 + o * 8 + jg]] : 0;
     }
-    const bool warp_live = warp * (JPW * OPT) < jcn;
-    float *wring = ring + warp * D * STAGE;
-    int32_t *wlist = wl + warp * kchunk;
+    const uint16_t *bx = bidx + bidx_off[g];
 
     float acc[OPT][G][NOUT][4];
 #pragma unroll
@@ -897,88 +906,85 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
 #pragma unroll
                 for (int x = 0; x < 4; ++x) acc[o][m][n][x] = 0.f;
 
-    for (int64_t k0 = 0; k0 < nk; k0 += kchunk) {
-        const int kn = (int)min((int64_t)kchunk, nk - k0);
-        __syncthreads();
-        // A's blocks: one thread per (k, row m, block row x), 16-byte stores
-        for (int t = tid; t < kn * G * 4; t += 128) {
-            const int x = t & 3, km = t >> 2;
-            const int kk = km / G, m = km - kk * G;
-            const int32_t q = __ldg(apos + (kb + k0 + kk) * G + m);
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (q >= 0) {
-                if (TA) {
-                    // row x of op(A) = column x of the stored block
-                    const float *p = a_val + __ldg(a_tr + q) * BS;
-                    v = make_float4(__ldg(p + x), __ldg(p + 4 + x), __ldg(p + 8 + x), __ldg(p + 12 + x));
-                } else {
-                    v = __ldg(reinterpret_cast<const float4 *>(a_val + (int64_t)q * BS) + x);
-                }
-            }
-            *reinterpret_cast<float4 *>(a_s + (size_t)km * BS + x * 4) = v;
-        }
-        for (int t = tid; t < kn; t += 128) {
-            uint32_t mm = 0;
-#pragma unroll
-            for (int m = 0; m < G; ++m) mm |= (__ldg(apos + (kb + k0 + t) * G + m) >= 0 ? 1u : 0u) << m;
-            msk[t] = mm;
-            brow[t] = TB ? 0 : b_rp[k_list[kb + k0 + t]];
-        }
-        // position-table tile [kn][JC], 16 bytes at a time, 0xFFFF past the group's columns
-        {
-            const uint16_t *bx = bidx + bidx_off[g];
-            for (int t = tid; t < kn * (JC / 8); t += 128) {
-                const int kk = t / (JC / 8), c = (t - kk * (JC / 8)) * 8;
-                uint4 w = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-                if (c < jcn) {
-                    w = __ldg(reinterpret_cast<const uint4 *>(bx + (k0 + kk) * nj_pad + j0 + c));
-                    if (c + 8 > jcn) {
-                        uint16_t e[8];
-                        memcpy(e, &w, 16);
-#pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            if (c + u >= jcn) e[u] = 0xFFFF;
-                        memcpy(&w, e, 16);
-                    }
-                }
-                *reinterpret_cast<uint4 *>(ixs + (size_t)kk * JC + c) = w;
-            }
-        }
-        __syncthreads();
-        if (!warp_live) continue;
-
-        // this warp's k list: entry = kk | (set mask << 16)
+    for (int64_t k0 = 0; k0 < nk; k0 += KC) {
+        const int kn = (int)min((int64_t)KC, nk - k0);
+        // list of this chunk's k's that hit any of the warp's columns
         int na = 0;
         for (int kq = 0; kq < kn; kq += 32) {
             const int kk = kq + lane;
             uint32_t om = 0;
+            uint32_t ixw[COLS / 2];
+            int4 ap = make_int4(-1, -1, -1, -1);
             if (kk < kn) {
-                const uint4 *row = reinterpret_cast<const uint4 *>(ixs + (size_t)kk * JC + warp * (JPW * OPT));
-                const uint4 v0 = row[0], v1 = row[1];
-                om = ((v0.x & v0.y & v0.z & v0.w) != 0xFFFFFFFFu ? 1u : 0u) |
-                     ((v1.x & v1.y & v1.z & v1.w) != 0xFFFFFFFFu ? 2u : 0u);
+                const uint16_t *row = bx + (k0 + kk) * nj_pad + j0;
+#pragma unroll
+                for (int p = 0; p < COLS / 8; ++p) {
+                    uint4 v = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+                    if (p * 8 < jcn) {
+                        v = __ldg(reinterpret_cast<const uint4 *>(row) + p);
+                        if (p * 8 + 8 > jcn) {
+                            uint16_t e[8];
+                            memcpy(e, &v, 16);
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (p * 8 + u >= jcn) e[u] = 0xFFFF;
+                            memcpy(&v, e, 16);
+                        }
+                    }
+                    ixw[p * 4 + 0] = v.x; ixw[p * 4 + 1] = v.y; ixw[p * 4 + 2] = v.z; ixw[p * 4 + 3] = v.w;
+                    if ((v.x & v.y & v.z & v.w) != 0xFFFFFFFFu) om |= 1u << p;
+                }
+                if (om) ap = __ldg(reinterpret_cast<const int4 *>(apos + (kb + k0 + kk) * G));
             }
             const unsigned b = __ballot_sync(0xffffffffu, om != 0);
-            if (om) wlist[na + __popc(b & ((1u << lane) - 1u))] = kk | (int)(om << 16);
+            if (om) {
+                int32_t *e = list + (size_t)(na + __popc(b & ((1u << lane) - 1u))) * EW;
+                const int32_t aq[4] = {ap.x, ap.y, ap.z, ap.w};
+                uint32_t mk = 0;
+#pragma unroll
+                for (int m = 0; m < G; ++m) {
+                    int32_t q = aq[m];
+                    if (q >= 0) {
+                        mk |= 1u << m;
+                        if (TA) q = (int32_t)__ldg(a_tr + q);
+                    }
+                    e[1 + m] = q;
+                }
+                e[0] = kk | (int)(om << 16) | (int)(mk << 24);
+                e[5] = TB ? 0 : (int32_t)b_rp[k_list[kb + k0 + kk]];
+                e[6] = 0;
+#pragma unroll
+                for (int w = 0; w < COLS / 2; ++w) e[7 + w] = (int32_t)ixw[w];
+            }
             na += __popc(b);
         }
         __syncwarp();
 
-        // copy list entry q into ring stage s (an empty commit group past the end)
+        static_assert((D & (D - 1)) == 0, "ring depth is a power of two");
+        // copy entry q into ring stage q % D (an empty commit group past the list's end)
         auto issue = [&](int q) {
             if (q < na) {
-                const int e = wlist[q], kk = e & 0xFFFF, om = e >> 16;
-                float *st = wring + (q % D) * STAGE;
+                const int32_t *e = list + (size_t)q * EW;
+                // the entry is the same for every lane: a broadcast keeps the tests warp-uniform
+                const int w0 = __shfl_sync(0xffffffffu, e[0], 0);
+                const int om = (w0 >> 16) & 0xFF, mk = (w0 >> 24) & 0xF;
+                float *st = ring + (q & (D - 1)) * STAGE;
+                if (lane < 16 && ((mk >> (lane >> 2)) & 1)) {
+                    const int m = lane >> 2, x = lane & 3;
+                    cp_async16(st + m * BS + x * 4, a_val + (int64_t)e[1 + m] * BS + x * 4, 16);
+                }
+                const int32_t brk = e[5];
 #pragma unroll
                 for (int o = 0; o < OPT; ++o) {
                     if (!((om >> o) & 1)) continue;
-                    const uint16_t ix = jv[o] ? ixs[(size_t)kk * JC + col[o]] : (uint16_t)0xFFFF;
-                    const bool hit = ix != 0xFFFF;
-                    const int64_t p = ((TB ? brj[o] : brow[kk]) + ix) * BS + r * 4;
+                    const int c = o * 8 + jg;
+                    const uint32_t ix = ((uint32_t)e[7 + (c >> 1)] >> ((c & 1) * 16)) & 0xFFFFu;
+                    const bool hit = ix != 0xFFFFu;
+                    const int64_t blk = hit ? (int64_t)(uint32_t)((TB ? brj[o] : brk) + (int32_t)ix) : 0;
 #pragma unroll
                     for (int n = 0; n < NOUT; ++n) {
                         const float *bv = n == 0 ? b_val1 : b_val2;
-                        cp_async16(st + ((o * NOUT + n) * JPW + jg) * SLOT + r * 4, hit ? bv + p : bv,
+                        cp_async16(st + G * BS + ((o * NOUT + n) * 8 + jg) * BS + prow * 4, bv + blk * BS + r * 4,
                                    hit ? 16 : 0);
                     }
                 }
@@ -991,37 +997,39 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
             issue(q + D - 1);
             cp_async_wait<D - 1>();
             __syncwarp();
-            const int e = wlist[q], kk = e & 0xFFFF, om = e >> 16;
-            const float *st = wring + (q % D) * STAGE;
-            const uint32_t mk = msk[kk];
-            // op(B)_kj column r of each (set, product): bv[o][n][z] = op(B)[z][r]
+            const int w0 = __shfl_sync(0xffffffffu, list[(size_t)q * EW], 0);
+            const int om = (w0 >> 16) & 0xFF, mk = (w0 >> 24) & 0xF;
+            const float *st = ring + (q & (D - 1)) * STAGE;
+            // bv[o][n][z] = op(B)[z][r]
             float bv[OPT][NOUT][4];
 #pragma unroll
             for (int o = 0; o < OPT; ++o) {
+                if (!((om >> o) & 1)) continue;
 #pragma unroll
                 for (int n = 0; n < NOUT; ++n) {
-                    const float *blk = st + ((o * NOUT + n) * JPW + jg) * SLOT;
-                    if (!((om >> o) & 1)) {
-#pragma unroll
-                        for (int z = 0; z < 4; ++z) bv[o][n][z] = 0.f;
-                    } else if (TB) {
-                        const float4 v = *reinterpret_cast<const float4 *>(blk + r * 4);
+                    const float *slot = st + G * BS + ((o * NOUT + n) * 8 + jg) * BS;
+                    if (TB) {
+                        const float4 v = *reinterpret_cast<const float4 *>(slot + prow * 4);
                         bv[o][n][0] = v.x; bv[o][n][1] = v.y; bv[o][n][2] = v.z; bv[o][n][3] = v.w;
                     } else {
 #pragma unroll
-                        for (int z = 0; z < 4; ++z) bv[o][n][z] = blk[z * 4 + r];
+                        for (int z = 0; z < 4; ++z) bv[o][n][z] = slot[((z + (jg >> 1)) & 3) * 4 + r];
                     }
                 }
             }
 #pragma unroll
             for (int m = 0; m < G; ++m) {
-                if (!((mk >> m) & 1u)) continue;
-                const float4 *am = reinterpret_cast<const float4 *>(a_s + ((size_t)kk * G + m) * BS);
-                float a[4][4];
+                if (!((mk >> m) & 1)) continue;
+                const float4 *am = reinterpret_cast<const float4 *>(st + m * BS);
+                float a[4][4];  // a[x][z] = op(A)_mk[x][z]
 #pragma unroll
-                for (int x = 0; x < 4; ++x) {
-                    const float4 v = am[x];
-                    a[x][0] = v.x; a[x][1] = v.y; a[x][2] = v.z; a[x][3] = v.w;
+                for (int y = 0; y < 4; ++y) {
+                    const float4 v = am[y];
+                    if (TA) {
+                        a[0][y] = v.x; a[1][y] = v.y; a[2][y] = v.z; a[3][y] = v.w;
+                    } else {
+                        a[y][0] = v.x; a[y][1] = v.y; a[y][2] = v.z; a[y][3] = v.w;
+                    }
                 }
 #pragma unroll
                 for (int o = 0; o < OPT; ++o) {
@@ -1038,13 +1046,14 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
             __syncwarp();
         }
         cp_async_wait<0>();
+        __syncwarp();
     }
 #pragma unroll
     for (int o = 0; o < OPT; ++o) {
         if (!jv[o]) continue;
 #pragma unroll
         for (int m = 0; m < G; ++m) {
-            const int32_t pos = cpos[(jb + j0 + col[o]) * G + m];
+            const int32_t pos = cpos[(jb + j0 + o * 8 + jg) * G + m];
             if (pos < 0) continue;
 #pragma unroll
             for (int n = 0; n < NOUT; ++n) {
@@ -1319,30 +1328,26 @@ template <int NOUT, bool TA, bool TB>
 lnv_status launch_gw(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1, const void *B2,
                      void *C1, void *C2)
 {
-    constexpr int G = 4, BS = 16, NW = 4, JC = 64, D = 3;
-    constexpr int SLOT = TB ? 16 : 20;
-    constexpr size_t ring = sizeof(float) * NW * D * 2 * NOUT * 8 * SLOT;
+    constexpr int D = 4, NW = 4;
+    using S = GwShape<NOUT, D, TA, TB>;
     const GroupPlan &gp = pl->grp;
     if (gp.n_groups == 0 || gp.max_j == 0) return LNV_OK;
     if (!gp.bidx && gp.candidates > 0) {
         set_error("row-group plan lacks the position table");
         return LNV_ERR_UNSUPPORTED;
     }
-    // four CTAs per SM: 228 KB of shared memory, 1 KB of it reserved per CTA
-    const size_t per_k = sizeof(float) * G * BS + sizeof(int64_t) + sizeof(uint16_t) * JC +
-                         sizeof(uint32_t) + sizeof(int32_t) * NW;
-    const size_t room = 228 * 1024 / 4 - 1024 - ring;
-    int kchunk = (int)std::min<size_t>(room / per_k, 65535);
-    kchunk = std::min(kchunk, (int)((std::max(gp.max_k, 1) + 7) & ~7));
-    kchunk &= ~7;  // keeps the position tile 16-byte aligned
-    const size_t smem = ring + (size_t)kchunk * per_k;
-    auto kern = k_gw<NOUT, D, TA, TB>;
+    if (gp.max_k > 0xFFFF || pl->B->nnzb >= ((int64_t)1 << 31)) {
+        set_error("row-group plan: more than 65535 k's in a group or 2^31 blocks in B");
+        return LNV_ERR_UNSUPPORTED;
+    }
+    const size_t smem = NW * S::warp_bytes;
+    auto kern = k_gw<NOUT, D, NW, TA, TB>;
     LNV_CUDA(ensure_smem((const void *)kern, smem));
     LNV_CUDA(prefer_smem((const void *)kern));
-    kern<<<group_grid(gp.n_groups, gp.max_j, JC), 128, smem, ctx->stream>>>(
-        gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list, gp.cpos, gp.bidx_off, gp.bidx, pl->A->tr,
+    kern<<<group_grid(gp.n_groups, gp.max_j, NW * S::COLS), NW * 32, smem, ctx->stream>>>(
+        gp.k_off, gp.apos, gp.j_off, gp.j_list, gp.cpos, gp.bidx_off, gp.bidx, gp.k_list, pl->A->tr,
         (const float *)A, pl->B->row_ptr, (const float *)B1, (const float *)B2, (float *)C1, (float *)C2,
-        kchunk, gp.n_groups);
+        gp.n_groups);
     LNV_LAUNCHED();
     return LNV_OK;
 }
