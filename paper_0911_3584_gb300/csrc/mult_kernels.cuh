@@ -834,28 +834,37 @@ __device__ __forceinline__ void cp_async_wait()
 // block-wide barrier: per chunk of KC k's of the group's K, the warp lists
 // the k's at which any of its columns holds op(B)_kj (one lane per k, ballot
 // compaction).  An entry carries k, a bitmask of the sets that hit, a bitmask
-// of the rows m holding A_mk, A's block positions and the 16-bit positions of
-// op(B)_kj for the warp's columns.  For each entry the warp copies A's blocks
-// (rows with A_mk only) and the stored rows of op(B)_kj (16 bytes per lane,
-// zero-filled at a miss) into a warp-private ring of D stages with cp.async,
-// D - 1 entries ahead of the one being multiplied.  Stored block rows are
-// columns of op(B) when op(B) = B^T, else lanes read column r across the four
-// rows of the block; the four rows of a block slot are rotated by (jg / 2) so
-// those column reads are free of bank conflicts.  A is read the same way:
-// rows of op(A), or of the stored block when op(A) = A^T.  Sums run over k in
-// ascending order (deterministic).  Outputs (m, j) outside C's pattern are
-// discarded at the store.
+// of the rows m holding A_mk, A's block positions and, per column, the block
+// index of op(B)_kj's stored block (-1 at a miss).  For each entry the warp
+// copies A's blocks (rows with A_mk only) and the stored rows of op(B)_kj
+// (16 bytes per lane, zero-filled at a miss) into a warp-private ring of D
+// stages with cp.async, D - 1 entries ahead of the one being multiplied.
+// Stored block rows are columns of op(B) when op(B) = B^T, else lanes read
+// column r across the four rows of the block; the four rows of a block slot
+// are rotated by (jg / 2) so those column reads are free of bank conflicts.
+// A is read the same way: rows of op(A), or of the stored block when
+// op(A) = A^T.  Sums run over k in ascending order (deterministic).  Outputs
+// (m, j) outside C's pattern are discarded at the store.
 template <int NOUT, int D, bool TA, bool TB>
 struct GwShape {
     static constexpr int G = 4, BS = 16, OPT = NOUT == 2 ? 2 : 4, COLS = 8 * OPT;
-    static constexpr int KC = NOUT == 2 ? 64 : 48;                 // k's per list chunk
-    // list entry: k | set mask << 16 | row mask << 24, A's four block positions,
-    // the row start of op(B)'s k when op(B) = B, a pad word, then the 16-bit
-    // positions of op(B)_kj for the warp's columns (odd size: no bank conflicts)
-    static constexpr int EW = 7 + COLS / 2;
+    // k's per list chunk: eight two-warp CTAs fit an SM's 228 KB of shared memory
+    static constexpr int KC = NOUT == 2 ? 48 : 30;
+    // list entry: k | set mask << 16 | row mask << 24, A's four block
+    // positions, then op(B)_kj's block index per column (odd size: the
+    // strided entry writes are free of bank conflicts)
+    static constexpr int EW = 5 + COLS;
     static constexpr int STAGE = G * BS + OPT * NOUT * 8 * BS;     // floats per ring stage
-    static constexpr size_t warp_bytes = sizeof(float) * D * STAGE + sizeof(int32_t) * KC * EW;
+    static constexpr size_t warp_bytes =
+        sizeof(float) * D * STAGE + sizeof(int32_t) * (KC * EW + COLS + 1);
 };
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16s(uint32_t dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
 
 template <int NOUT, int D, int NW, bool TA, bool TB>
 __global__ void __launch_bounds__(NW * 32, 16 / NW)
@@ -871,11 +880,13 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
     using S = GwShape<NOUT, D, TA, TB>;
     constexpr int G = S::G, BS = S::BS, OPT = S::OPT, COLS = S::COLS, KC = S::KC, EW = S::EW;
     constexpr int STAGE = S::STAGE;
+    static_assert((D & (D - 1)) == 0, "ring depth is a power of two");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *ring = reinterpret_cast<float *>(smem_raw) + (size_t)warp * D * STAGE;                 // [D][STAGE]
     int32_t *list = reinterpret_cast<int32_t *>(reinterpret_cast<float *>(smem_raw) + (size_t)NW * D * STAGE) +
-                    (size_t)warp * KC * EW;                                                       // [KC][EW]
+                    (size_t)warp * (KC * EW + COLS + 1);                                          // [KC][EW]
+    int32_t *rowj = list + KC * EW;                                                               // [COLS]
 
     const int64_t g = grp_of_block();
     if (g >= n_groups) return;
@@ -886,15 +897,21 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
     if (j0 >= nj) return;
     const int jcn = (int)min((int64_t)COLS, nj - j0);
     const int jg = lane >> 2, r = lane & 3;
-    const int prow = (r + (jg >> 1)) & 3;  // rotated slot row of stored row r
-    int32_t brj[OPT];  // row start of op(B)'s column j when op(B) = B^T
-    bool jv[OPT];
-#pragma unroll
-    for (int o = 0; o < OPT; ++o) {
-        jv[o] = o * 8 + jg < jcn;
-        brj[o] = (TB && jv[o]) ? (int32_t)b_rp[j_list[jb + j0 + o * 8 + jg]] : 0;
-    }
+    // op(B) = B^T: row start of the stored row j for each of the warp's columns
+    if (TB)
+        for (int c = lane; c < COLS; c += 32) rowj[c] = c < jcn ? (int32_t)b_rp[j_list[jb + j0 + c]] : 0;
     const uint16_t *bx = bidx + bidx_off[g];
+
+    // per-lane shared-memory offsets (bytes) inside a ring stage
+    const uint32_t ring0 = smem_addr(ring);
+    const int rot = jg >> 1;
+    const uint32_t b_dst = (uint32_t)(G * BS + jg * BS + ((r + rot) & 3) * 4) * 4u;   // copy of stored row r
+    uint32_t b_rd[4];                                                                // stored row z, column r
+#pragma unroll
+    for (int z = 0; z < 4; ++z) b_rd[z] = (uint32_t)(G * BS + jg * BS + ((z + rot) & 3) * 4 + r) * 4u;
+    const uint32_t a_dst = (uint32_t)((lane >> 2) * BS + (lane & 3) * 4) * 4u;
+    const float *a_src = a_val + (lane & 3) * 4;
+    const float *b_src1 = b_val1 + r * 4, *b_src2 = (NOUT == 2 ? b_val2 : b_val1) + r * 4;
 
     float acc[OPT][G][NOUT][4];
 #pragma unroll
@@ -908,13 +925,13 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
 
     for (int64_t k0 = 0; k0 < nk; k0 += KC) {
         const int kn = (int)min((int64_t)KC, nk - k0);
+        __syncwarp();
         // list of this chunk's k's that hit any of the warp's columns
         int na = 0;
         for (int kq = 0; kq < kn; kq += 32) {
             const int kk = kq + lane;
             uint32_t om = 0;
             uint32_t ixw[COLS / 2];
-            int4 ap = make_int4(-1, -1, -1, -1);
             if (kk < kn) {
                 const uint16_t *row = bx + (k0 + kk) * nj_pad + j0;
 #pragma unroll
@@ -934,11 +951,11 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
                     ixw[p * 4 + 0] = v.x; ixw[p * 4 + 1] = v.y; ixw[p * 4 + 2] = v.z; ixw[p * 4 + 3] = v.w;
                     if ((v.x & v.y & v.z & v.w) != 0xFFFFFFFFu) om |= 1u << p;
                 }
-                if (om) ap = __ldg(reinterpret_cast<const int4 *>(apos + (kb + k0 + kk) * G));
             }
             const unsigned b = __ballot_sync(0xffffffffu, om != 0);
             if (om) {
                 int32_t *e = list + (size_t)(na + __popc(b & ((1u << lane) - 1u))) * EW;
+                const int4 ap = __ldg(reinterpret_cast<const int4 *>(apos + (kb + k0 + kk) * G));
                 const int32_t aq[4] = {ap.x, ap.y, ap.z, ap.w};
                 uint32_t mk = 0;
 #pragma unroll
@@ -951,16 +968,17 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
                     e[1 + m] = q;
                 }
                 e[0] = kk | (int)(om << 16) | (int)(mk << 24);
-                e[5] = TB ? 0 : (int32_t)b_rp[k_list[kb + k0 + kk]];
-                e[6] = 0;
+                const int32_t brk = TB ? 0 : (int32_t)b_rp[k_list[kb + k0 + kk]];
 #pragma unroll
-                for (int w = 0; w < COLS / 2; ++w) e[7 + w] = (int32_t)ixw[w];
+                for (int c = 0; c < COLS; ++c) {
+                    const uint32_t ix = (ixw[c >> 1] >> ((c & 1) * 16)) & 0xFFFFu;
+                    e[5 + c] = ix == 0xFFFFu ? -1 : (TB ? rowj[c] : brk) + (int32_t)ix;
+                }
             }
             na += __popc(b);
         }
         __syncwarp();
 
-        static_assert((D & (D - 1)) == 0, "ring depth is a power of two");
         // copy entry q into ring stage q % D (an empty commit group past the list's end)
         auto issue = [&](int q) {
             if (q < na) {
@@ -968,25 +986,18 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
                 // the entry is the same for every lane: a broadcast keeps the tests warp-uniform
                 const int w0 = __shfl_sync(0xffffffffu, e[0], 0);
                 const int om = (w0 >> 16) & 0xFF, mk = (w0 >> 24) & 0xF;
-                float *st = ring + (q & (D - 1)) * STAGE;
-                if (lane < 16 && ((mk >> (lane >> 2)) & 1)) {
-                    const int m = lane >> 2, x = lane & 3;
-                    cp_async16(st + m * BS + x * 4, a_val + (int64_t)e[1 + m] * BS + x * 4, 16);
-                }
-                const int32_t brk = e[5];
+                const uint32_t st = ring0 + (uint32_t)((q & (D - 1)) * STAGE * 4);
+                if (lane < 16 && ((mk >> (lane >> 2)) & 1))
+                    cp_async16s(st + a_dst, a_src + (int64_t)e[1 + (lane >> 2)] * BS, 16);
 #pragma unroll
                 for (int o = 0; o < OPT; ++o) {
                     if (!((om >> o) & 1)) continue;
-                    const int c = o * 8 + jg;
-                    const uint32_t ix = ((uint32_t)e[7 + (c >> 1)] >> ((c & 1) * 16)) & 0xFFFFu;
-                    const bool hit = ix != 0xFFFFu;
-                    const int64_t blk = hit ? (int64_t)(uint32_t)((TB ? brj[o] : brk) + (int32_t)ix) : 0;
-#pragma unroll
-                    for (int n = 0; n < NOUT; ++n) {
-                        const float *bv = n == 0 ? b_val1 : b_val2;
-                        cp_async16(st + G * BS + ((o * NOUT + n) * 8 + jg) * BS + prow * 4, bv + blk * BS + r * 4,
-                                   hit ? 16 : 0);
-                    }
+                    const int32_t blk = e[5 + o * 8 + jg];
+                    const int bytes = blk >= 0 ? 16 : 0;
+                    const int64_t off = (int64_t)max(blk, 0) * BS;
+                    cp_async16s(st + b_dst + (uint32_t)(o * NOUT * 8 * BS * 4), b_src1 + off, bytes);
+                    if (NOUT == 2)
+                        cp_async16s(st + b_dst + (uint32_t)((o * NOUT + 1) * 8 * BS * 4), b_src2 + off, bytes);
                 }
             }
             cp_async_commit();
@@ -999,7 +1010,7 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
             __syncwarp();
             const int w0 = __shfl_sync(0xffffffffu, list[(size_t)q * EW], 0);
             const int om = (w0 >> 16) & 0xFF, mk = (w0 >> 24) & 0xF;
-            const float *st = ring + (q & (D - 1)) * STAGE;
+            const unsigned char *st = reinterpret_cast<const unsigned char *>(ring) + (q & (D - 1)) * STAGE * 4;
             // bv[o][n][z] = op(B)[z][r]
             float bv[OPT][NOUT][4];
 #pragma unroll
@@ -1007,20 +1018,20 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
                 if (!((om >> o) & 1)) continue;
 #pragma unroll
                 for (int n = 0; n < NOUT; ++n) {
-                    const float *slot = st + G * BS + ((o * NOUT + n) * 8 + jg) * BS;
+                    const unsigned char *slot = st + (o * NOUT + n) * 8 * BS * 4;
                     if (TB) {
-                        const float4 v = *reinterpret_cast<const float4 *>(slot + prow * 4);
+                        const float4 v = *reinterpret_cast<const float4 *>(slot + b_dst);
                         bv[o][n][0] = v.x; bv[o][n][1] = v.y; bv[o][n][2] = v.z; bv[o][n][3] = v.w;
                     } else {
 #pragma unroll
-                        for (int z = 0; z < 4; ++z) bv[o][n][z] = slot[((z + (jg >> 1)) & 3) * 4 + r];
+                        for (int z = 0; z < 4; ++z) bv[o][n][z] = *reinterpret_cast<const float *>(slot + b_rd[z]);
                     }
                 }
             }
 #pragma unroll
             for (int m = 0; m < G; ++m) {
                 if (!((mk >> m) & 1)) continue;
-                const float4 *am = reinterpret_cast<const float4 *>(st + m * BS);
+                const float4 *am = reinterpret_cast<const float4 *>(st) + m * 4;
                 float a[4][4];  // a[x][z] = op(A)_mk[x][z]
 #pragma unroll
                 for (int y = 0; y < 4; ++y) {
@@ -1046,11 +1057,10 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
             __syncwarp();
         }
         cp_async_wait<0>();
-        __syncwarp();
     }
 #pragma unroll
     for (int o = 0; o < OPT; ++o) {
-        if (!jv[o]) continue;
+        if (o * 8 + jg >= jcn) continue;
 #pragma unroll
         for (int m = 0; m < G; ++m) {
             const int32_t pos = cpos[(jb + j0 + o * 8 + jg) * G + m];
@@ -1328,7 +1338,7 @@ template <int NOUT, bool TA, bool TB>
 lnv_status launch_gw(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1, const void *B2,
                      void *C1, void *C2)
 {
-    constexpr int D = 4, NW = 4;
+    constexpr int D = 4, NW = 2;
     using S = GwShape<NOUT, D, TA, TB>;
     const GroupPlan &gp = pl->grp;
     if (gp.n_groups == 0 || gp.max_j == 0) return LNV_OK;
@@ -1341,6 +1351,7 @@ lnv_status launch_gw(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void
         return LNV_ERR_UNSUPPORTED;
     }
     const size_t smem = NW * S::warp_bytes;
+    static_assert(8 * (NW * S::warp_bytes + 1024) <= 228 * 1024, "eight CTAs per SM");
     auto kern = k_gw<NOUT, D, NW, TA, TB>;
     LNV_CUDA(ensure_smem((const void *)kern, smem));
     LNV_CUDA(prefer_smem((const void *)kern));
