@@ -186,6 +186,30 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
                             cpos[(size_t)(j_off[g] + jl) * G + m] = (int32_t)q;
                         }
                     }
+                    // Order J by the set of the group's rows whose C row holds j (then by
+                    // index): consecutive columns then need the same rows, so a kernel
+                    // can skip the rows that no column of a set keeps.
+                    {
+                        const int64_t nj_g = nj[g];
+                        std::vector<int32_t> key(nj_g), perm(nj_g);
+                        for (int64_t jl = 0; jl < nj_g; ++jl) {
+                            int cm = 0;
+                            for (int m = 0; m < G; ++m)
+                                if (cpos[(size_t)(j_off[g] + jl) * G + m] >= 0) cm |= 1 << m;
+                            key[jl] = cm;
+                            perm[jl] = (int32_t)jl;
+                        }
+                        std::stable_sort(perm.begin(), perm.end(),
+                                         [&](int32_t a, int32_t b) { return key[a] > key[b]; });
+                        std::vector<int32_t> jl_new(nj_g), cp_new((size_t)nj_g * G);
+                        for (int64_t t = 0; t < nj_g; ++t) {
+                            jl_new[t] = j_list[j_off[g] + perm[t]];
+                            for (int m = 0; m < G; ++m)
+                                cp_new[(size_t)t * G + m] = cpos[(size_t)(j_off[g] + perm[t]) * G + m];
+                        }
+                        std::copy(jl_new.begin(), jl_new.end(), j_list.begin() + j_off[g]);
+                        std::copy(cp_new.begin(), cp_new.end(), cpos.begin() + (size_t)j_off[g] * G);
+                    }
                     std::vector<int32_t>().swap(Ks[g]);
                     std::vector<int32_t>().swap(Js[g]);
                 }

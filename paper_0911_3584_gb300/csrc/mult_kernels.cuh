@@ -912,6 +912,18 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
     const uint32_t a_dst = (uint32_t)((lane >> 2) * BS + (lane & 3) * 4) * 4u;
     const float *a_src = a_val + (lane & 3) * 4;
     const float *b_src1 = b_val1 + r * 4, *b_src2 = (NOUT == 2 ? b_val2 : b_val1) + r * 4;
+    // need: for each set o, bits (4 o + m) for the rows m whose C row holds one
+    // of the set's columns; rows outside it are never multiplied for the set
+    uint32_t need = 0;
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+        uint32_t cm = 0;
+        if (o * 8 + jg < jcn) {
+            const int4 cp = __ldg(reinterpret_cast<const int4 *>(cpos + (jb + j0 + o * 8 + jg) * G));
+            cm = (cp.x >= 0 ? 1u : 0u) | (cp.y >= 0 ? 2u : 0u) | (cp.z >= 0 ? 4u : 0u) | (cp.w >= 0 ? 8u : 0u);
+        }
+        need |= __reduce_or_sync(0xffffffffu, cm) << (4 * o);
+    }
 
     float acc[OPT][G][NOUT][4];
 #pragma unroll
@@ -930,9 +942,12 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
         int na = 0;
         for (int kq = 0; kq < kn; kq += 32) {
             const int kk = kq + lane;
-            uint32_t om = 0;
+            uint32_t om = 0, mk = 0;
             uint32_t ixw[COLS / 2];
+            int4 ap = make_int4(-1, -1, -1, -1);
             if (kk < kn) {
+                ap = __ldg(reinterpret_cast<const int4 *>(apos + (kb + k0 + kk) * G));
+                mk = (ap.x >= 0 ? 1u : 0u) | (ap.y >= 0 ? 2u : 0u) | (ap.z >= 0 ? 4u : 0u) | (ap.w >= 0 ? 8u : 0u);
                 const uint16_t *row = bx + (k0 + kk) * nj_pad + j0;
 #pragma unroll
                 for (int p = 0; p < COLS / 8; ++p) {
@@ -949,22 +964,23 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
                         }
                     }
                     ixw[p * 4 + 0] = v.x; ixw[p * 4 + 1] = v.y; ixw[p * 4 + 2] = v.z; ixw[p * 4 + 3] = v.w;
-                    if ((v.x & v.y & v.z & v.w) != 0xFFFFFFFFu) om |= 1u << p;
+                    // a set counts when it holds a block and one of its needed rows has A_mk
+                    if ((v.x & v.y & v.z & v.w) != 0xFFFFFFFFu && ((need >> (4 * p)) & mk)) om |= 1u << p;
                 }
+                uint32_t used = 0;
+#pragma unroll
+                for (int o = 0; o < OPT; ++o)
+                    if ((om >> o) & 1) used |= need >> (4 * o);
+                mk &= used;
             }
             const unsigned b = __ballot_sync(0xffffffffu, om != 0);
             if (om) {
                 int32_t *e = list + (size_t)(na + __popc(b & ((1u << lane) - 1u))) * EW;
-                const int4 ap = __ldg(reinterpret_cast<const int4 *>(apos + (kb + k0 + kk) * G));
                 const int32_t aq[4] = {ap.x, ap.y, ap.z, ap.w};
-                uint32_t mk = 0;
 #pragma unroll
                 for (int m = 0; m < G; ++m) {
                     int32_t q = aq[m];
-                    if (q >= 0) {
-                        mk |= 1u << m;
-                        if (TA) q = (int32_t)__ldg(a_tr + q);
-                    }
+                    if (TA && ((mk >> m) & 1)) q = (int32_t)__ldg(a_tr + q);
                     e[1 + m] = q;
                 }
                 e[0] = kk | (int)(om << 16) | (int)(mk << 24);
@@ -1044,7 +1060,7 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
                 }
 #pragma unroll
                 for (int o = 0; o < OPT; ++o) {
-                    if (!((om >> o) & 1)) continue;
+                    if (!((om >> o) & 1) || !((need >> (4 * o + m)) & 1)) continue;
 #pragma unroll
                     for (int z = 0; z < 4; ++z)
 #pragma unroll
