@@ -134,11 +134,15 @@ lnv_status lnv_plan_product(lnv_ctx *ctx, const lnv_pattern *A, const lnv_patter
  * a cp.async shared-memory ring of op(B) blocks (FP32 values, NSF = 4; other
  * cases run kernel 3), 6 row groups on tensor cores (mma.sync TF32 with
  * a hi/lo split of both operands, FP32 accumulation; FP32 values, NSF = 4;
- * other cases run kernel 3).
+ * other cases run kernel 3), 7 listed triples: per block of C the stored
+ * (op(A)_ik, op(B)_kj) pairs, k ascending, listed once per plan (NSF = 4;
+ * other NSF run kernel 0).
  * The default is 3 when at least half of the table's candidates hit, else 4,
  * when the tables fit a third of the free device memory. */
 lnv_status lnv_plan_info(const lnv_plan *plan, int64_t *triples, int *mode);
-/* Select the kernel of a plan (0..6 as above); all give the same result up
+/* Number of product kernels (0 .. LNV_NUM_KERNELS - 1). */
+#define LNV_NUM_KERNELS 8
+/* Select the kernel of a plan (0..7 as above); all give the same result up
  * to rounding order.  Kernels 3-5 build their tables on first selection
  * (allocates, synchronises).  LNV_ERR_UNSUPPORTED if the kernel cannot run
  * this plan. */
@@ -211,8 +215,9 @@ lnv_status lnv_system_set_stage_kernel(lnv_ctx *ctx, lnv_system *sys, int stage,
 /* Autotuner: runs one evaluation on S, H, L, then times every applicable
  * kernel of each product stage (XY, TU, Z, Q, W) on those intermediates
  * (reps launches each, CUDA events on the context stream) and keeps the
- * fastest.  ms_out (5 x 7 values, may be NULL) receives the time of every
- * (stage, kernel) pair tried, -1 for kernels that do not apply.  Allocates and synchronises; results do not change beyond rounding
+ * fastest.  ms_out (5 x LNV_NUM_KERNELS values, may be NULL) receives the
+ * time of every (stage, kernel) pair tried, -1 for kernels that do not
+ * apply.  Allocates and synchronises; results do not change beyond rounding
  * order.  Uses the system's own workspace. */
 lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev, const void *H_dev,
                                const void *L_dev, int reps, double *ms_out);

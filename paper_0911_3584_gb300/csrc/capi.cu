@@ -477,13 +477,15 @@ lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
         const int orig = sg.pl->mode;
         int best = orig;
         float best_ms = 1e30f;
-        for (int k = 0; k < 7; ++k)
-            if (ms_out) ms_out[si * 7 + k] = -1.0;
-        for (int k : {0, 2, 3, 4, 5, 6}) {
+        for (int k = 0; k < LNV_NUM_KERNELS; ++k)
+            if (ms_out) ms_out[si * LNV_NUM_KERNELS + k] = -1.0;
+        for (int k : {0, 2, 3, 4, 5, 6, 7}) {
             // per-warp ring kernel: FP32 values, NSF = 4 (elsewhere kernel 5 is kernel 3)
             if (k == 5 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
             // tensor-core kernel: FP32 values, NSF = 4 (3xTF32, FP32-level accuracy)
             if (k == 6 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
+            // listed triples: NSF = 4 (elsewhere kernel 7 is kernel 0)
+            if (k == 7 && sys->nsf != 4) continue;
             if (plan_set_kernel(ctx, sg.pl, k) != LNV_OK) continue;
             lnv_status rs = multiply2(ctx, sg.pl, sys->nsf, sys->prec, sg.A, sg.B1, sg.B2, sg.C1, sg.C2);
             if (rs == LNV_OK && cudaEventRecord(e0, ctx->stream) == cudaSuccess) {
@@ -493,7 +495,7 @@ lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
                 if (rs == LNV_OK && cudaEventRecord(e1, ctx->stream) == cudaSuccess &&
                     cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
                     ms /= reps;
-                    if (ms_out) ms_out[si * 7 + k] = ms;
+                    if (ms_out) ms_out[si * LNV_NUM_KERNELS + k] = ms;
                     if (ms < best_ms) {
                         best_ms = ms;
                         best = k;

@@ -104,14 +104,29 @@ struct GroupPlan {
     size_t bytes = 0;
 };
 
+// Triple-list plan of a product (see triples.cu): C's blocks as work items,
+// ordered by groups of 4 rows, then column, then row inside the group; for
+// each item the contributing (op(A)_ik, op(B)_kj) storage positions, k
+// ascending.
+struct TriplePlan {
+    int64_t n_items = 0;
+    int32_t *item_cb = nullptr;  // [n_items]     C block of the item
+    int64_t *t_off = nullptr;    // [n_items + 1] item's range in tri
+    int2 *tri = nullptr;         // [triples]     (A block, B block) storage positions
+    size_t bytes = 0;
+};
+
 struct lnv_plan {
     const lnv_pattern *A, *B, *C;
     int trans_a, trans_b;
     // 0 push (row gather into a shared-memory row accumulator), 1 pull with a
     // binary search per k, 2 pull with a merge-join walk (symmetric B pattern),
-    // 3 row groups with a dense position table, 4 row groups with hit lists
+    // 3 row groups with a dense position table, 4 row groups with hit lists,
+    // 5 row groups with per-warp lists, 6 row groups on tensor cores, 7
+    // listed triples per output block
     int mode;
     GroupPlan grp;
+    TriplePlan tri;
     // work items (row, first output slot) of the merge-join pull, for 64 and
     // 128 outputs per CTA (device arrays)
     int2 *items64 = nullptr, *items128 = nullptr;
@@ -151,6 +166,9 @@ lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_byt
                             bool sparse);
 lnv_status scan_exclusive(cudaStream_t st, const int64_t *in, int64_t n, int64_t *out);
 void group_plan_free(GroupPlan *gp);
+// Triple-list plan (triples.cu); LNV_ERR_UNSUPPORTED when it would not fit the budget.
+lnv_status triple_plan_build(lnv_ctx *ctx, lnv_plan *pl, size_t budget_bytes);
+void triple_plan_free(TriplePlan *tp);
 lnv_status pattern_host_cols(lnv_ctx *ctx, const lnv_pattern *p);
 lnv_status multiply(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec, const void *A,
                     const void *B, void *C);

@@ -194,7 +194,7 @@ lnv_status plan_pull_items(lnv_plan *pl)
 
 lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
 {
-    LNV_ARG(pl && kernel >= 0 && kernel <= 6, "kernel must be 0..6");
+    LNV_ARG(pl && kernel >= 0 && kernel < LNV_NUM_KERNELS, "kernel must be 0..7");
     if (kernel == 2) {
         if (!pl->B->symmetric) {
             set_error("the merge-join pull needs a symmetric B pattern");
@@ -202,7 +202,11 @@ lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
         }
         LNV_TRY(plan_pull_items(pl));
     }
-    if (kernel >= 3) {
+    if (kernel == 7) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        LNV_TRY(triple_plan_build(ctx, pl, free_b / 3));
+    } else if (kernel >= 3) {
         // build the row-group form this kernel reads, if missing
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
@@ -214,6 +218,7 @@ lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
 
 void plan_trim(lnv_plan *plan)
 {
+    if (plan->mode != 7) triple_plan_free(&plan->tri);
     GroupPlan &gp = plan->grp;
     const bool dense = plan->mode == 3 || plan->mode == 5 || plan->mode == 6, sparse = plan->mode == 4;
     if (!dense && !sparse) {
@@ -236,6 +241,7 @@ void plan_free(lnv_plan *plan)
     cudaFree(plan->items64);
     cudaFree(plan->items128);
     group_plan_free(&plan->grp);
+    triple_plan_free(&plan->tri);
     delete plan;
 }
 

@@ -1091,6 +1091,83 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
     }
 }
 
+// ------------------------------------------------------------------ listed triples
+
+// Output-stationary product over listed triples (NSF = 4).  Four lanes own one
+// block of C (an item of the triple-list plan) and lane x keeps row x of it
+// for the NOUT products in registers.  For each listed (op(A)_ik, op(B)_kj)
+// pair, k ascending, the lane reads row x of op(A)_ik and the whole block
+// op(B)_kj (the group's four lanes read the same addresses) and adds their
+// product; the next pair's blocks are fetched while the current ones are
+// applied.  Nothing is multiplied that is absent or discarded.  Items are
+// ordered by groups of four rows, then column, so the warps that run together
+// share most blocks and hit in L1.
+template <typename T, int NOUT, bool TA, bool TB>
+__global__ void __launch_bounds__(128)
+k_tri(int64_t n_items, const int32_t *__restrict__ item_cb, const int64_t *__restrict__ t_off,
+      const int2 *__restrict__ tri, const T *__restrict__ a_val, const T *__restrict__ b_val1,
+      const T *__restrict__ b_val2, T *__restrict__ c_val1, T *__restrict__ c_val2)
+{
+    constexpr int BS = 16;
+    const int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2;
+    const int x = threadIdx.x & 3;
+    if (it >= n_items) return;
+    const int64_t t0 = t_off[it], t1 = t_off[it + 1];
+    T acc[NOUT][4];
+#pragma unroll
+    for (int n = 0; n < NOUT; ++n)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[n][y] = T(0);
+    // a[z] = op(A)_ik[x][z]; b[n][z][y] = stored block of op(B)_kj, row z
+    auto load = [&](int64_t t, T (&a)[4], T (&b)[NOUT][4][4]) {
+        const int2 p = __ldg(tri + t);
+        const T *ab = a_val + (int64_t)p.x * BS;
+        if (TA) {
+#pragma unroll
+            for (int z = 0; z < 4; ++z) a[z] = __ldg(ab + z * 4 + x);
+        } else {
+            ld_row<T, 4>(ab + x * 4, a, true);
+        }
+#pragma unroll
+        for (int n = 0; n < NOUT; ++n) {
+            const T *bb = (n == 0 ? b_val1 : b_val2) + (int64_t)p.y * BS;
+#pragma unroll
+            for (int z = 0; z < 4; ++z) ld_row<T, 4>(bb + z * 4, b[n][z], true);
+        }
+    };
+    auto apply = [&](const T (&a)[4], const T (&b)[NOUT][4][4]) {
+#pragma unroll
+        for (int n = 0; n < NOUT; ++n)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                T s = acc[n][y];
+#pragma unroll
+                for (int z = 0; z < 4; ++z) s = fma(a[z], TB ? b[n][y][z] : b[n][z][y], s);
+                acc[n][y] = s;
+            }
+    };
+    T a0[4], a1[4], b0[NOUT][4][4], b1[NOUT][4][4];
+    if (t0 < t1) load(t0, a0, b0);
+    for (int64_t t = t0; t < t1; t += 2) {
+        if (t + 1 < t1) load(t + 1, a1, b1);
+        apply(a0, b0);
+        if (t + 1 >= t1) break;
+        if (t + 2 < t1) load(t + 2, a0, b0);
+        apply(a1, b1);
+    }
+    const int64_t cb = item_cb[it];
+#pragma unroll
+    for (int n = 0; n < NOUT; ++n) {
+        T *dst = (n == 0 ? c_val1 : c_val2) + cb * BS + x * 4;
+        if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(acc[n][0], acc[n][1], acc[n][2], acc[n][3]);
+        } else {
+            reinterpret_cast<double2 *>(dst)[0] = make_double2(acc[n][0], acc[n][1]);
+            reinterpret_cast<double2 *>(dst)[1] = make_double2(acc[n][2], acc[n][3]);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ row groups on tensor cores
 
 __device__ __forceinline__ uint32_t to_tf32(float f)
@@ -1404,6 +1481,23 @@ lnv_status launch_gmma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const vo
     return LNV_OK;
 }
 
+template <typename T, int NOUT, bool TA, bool TB>
+lnv_status launch_tri(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1, const void *B2,
+                      void *C1, void *C2)
+{
+    const TriplePlan &tp = pl->tri;
+    if (tp.n_items == 0) return LNV_OK;
+    if (!tp.t_off || (!tp.tri && pl->triples > 0)) {
+        set_error("plan lacks its triple lists");
+        return LNV_ERR_UNSUPPORTED;
+    }
+    const int64_t threads = tp.n_items * 4;
+    k_tri<T, NOUT, TA, TB><<<(unsigned)((threads + 127) / 128), 128, 0, ctx->stream>>>(
+        tp.n_items, tp.item_cb, tp.t_off, tp.tri, (const T *)A, (const T *)B1, (const T *)B2, (T *)C1, (T *)C2);
+    LNV_LAUNCHED();
+    return LNV_OK;
+}
+
 template <typename T, int NSF, int NOUT, bool TA, bool TB>
 lnv_status launch_group(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
                         const void *B2, void *C1, void *C2)
@@ -1495,6 +1589,19 @@ template <typename T, int NSF, bool TA, bool TB>
 lnv_status dispatch_mode(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
                          const void *B2, void *C1, void *C2)
 {
+    if (pl->mode == 7) {
+        if constexpr (NSF == 4) {
+            // two fused FP32 products; FP64 runs them one at a time (registers)
+            if (B2 && sizeof(T) == 4) return launch_tri<T, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
+            LNV_TRY((launch_tri<T, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr)));
+            if (B2) LNV_TRY((launch_tri<T, 1, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr)));
+            return LNV_OK;
+        } else {
+            // other block sizes: the push kernel, which needs no tables
+            if (B2) return launch_push2<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
+            return launch_push2<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr);
+        }
+    }
     if (pl->mode >= 3) {
         if (B2) return launch_group<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
         return launch_group<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr);

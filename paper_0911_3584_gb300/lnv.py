@@ -246,7 +246,7 @@ class Plan:
         _check(lib().lnv_plan_info(self.h, ctypes.byref(t), ctypes.byref(m)), "lnv_plan_info")
         self.triples, self.mode = t.value, self.KERNELS[m.value]
 
-    KERNELS = ("push", "pull", "pull-merge", "group", "group-sparse", "group-pipe", "group-mma")
+    KERNELS = ("push", "pull", "pull-merge", "group", "group-sparse", "group-pipe", "group-mma", "triples")
 
     def set_kernel(self, kernel):
         k = self.KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)
@@ -421,10 +421,11 @@ class System:
         s = _vals(S, self.P_sh, self.nsf, self.prec, "S")
         h = _vals(H, self.P_sh, self.nsf, self.prec, "H")
         l_ = _vals(L, self.P_l, self.nsf, self.prec, "L")
-        ms = (ctypes.c_double * 35)()
+        nk = len(Plan.KERNELS)
+        ms = (ctypes.c_double * (5 * nk))()
         _check(lib().lnv_system_autotune(self.ctx.h, self.h, s, h, l_, int(reps), ms), "lnv_system_autotune")
         ks = self.stage_kernels()
-        self.tune_table = {st: {Plan.KERNELS[k]: ms[i * 7 + k] for k in range(7) if ms[i * 7 + k] >= 0}
+        self.tune_table = {st: {Plan.KERNELS[k]: ms[i * nk + k] for k in range(nk) if ms[i * nk + k] >= 0}
                            for i, st in enumerate(("XY", "TU", "Z", "Q", "W"))}
         return {st: (ks[st], self.tune_table[st][ks[st]]) for st in self.tune_table}
 

@@ -109,7 +109,7 @@ PRODUCT_CASES = [
 
 
 @pytest.mark.parametrize("kernel", ["default", "push", "pull", "pull-merge", "group", "group-sparse",
-                                    "group-pipe", "group-mma"])
+                                    "group-pipe", "group-mma", "triples"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("nsf", [1, 2, 4, 9])
 @pytest.mark.parametrize("case", PRODUCT_CASES)
