@@ -229,16 +229,19 @@ lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
 lnv_status lnv_system_profile(lnv_system *sys, int enable);
 lnv_status lnv_system_stage_ms(lnv_system *sys, double *ms7);
 
-/* One evaluation.  S_dev, H_dev (on the r_sh pattern) and L_dev (on the r_l
- * pattern) are value arrays in the system's precision.  Writes, per system
- * s, out_dev[6 s + 0..5] = {E, N_e, Tr[LSLH], Tr[LSLSLH], Tr[LSLS],
- * Tr[LSLSLS]} (FP64), and, when G_dev is not NULL, dE/dL on L's pattern in
- * the system's precision.  Workspace: ws_dev of ws_bytes >=
- * lnv_system_workspace_size, or NULL to use a buffer the system allocates
- * on first use and keeps.  Asynchronous on the context stream. */
+/* One evaluation (Sec. 2, Eq. 3).  S_dev, H_dev (on the r_sh pattern) and
+ * L_dev (on the r_l pattern) are value arrays in the system's precision.
+ * Writes, per system s, out_dev[6 s + 0..5] = {E, N_e, Tr[LSLH],
+ * Tr[LSLSLH], Tr[LSLS], Tr[LSLSLS]} (FP64); when G_dev is not NULL, dE/dL
+ * = 6(SLH + HLS) - 4(SLSLH + SLHLS + HLSLS) on L's pattern; when GN_dev is
+ * not NULL, dN_e/dL = 12(SLS - SLSLS) on L's pattern (both in the system's
+ * precision, FP64-combined, every stored entry of L independent).
+ * Workspace: ws_dev of ws_bytes >= lnv_system_workspace_size(with_grad =
+ * G_dev != NULL), or NULL to use a buffer the system allocates on first use
+ * and keeps.  Asynchronous on the context stream. */
 lnv_status lnv_energy_grad(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
                            const void *H_dev, const void *L_dev, double *out_dev,
-                           void *G_dev, void *ws_dev, size_t ws_bytes);
+                           void *G_dev, void *GN_dev, void *ws_dev, size_t ws_bytes);
 
 #ifdef __cplusplus
 }

@@ -177,7 +177,7 @@ def transpose(M: dict) -> dict:
 
 
 def lnv_energy_grad(pos, cell, r_sh, r_l, S: dict, H: dict, L: dict, grad: bool = True,
-                    keep: bool = False) -> dict:
+                    keep: bool = False, grad_ne: bool = False) -> dict:
     """E, N_e and dE/dL of the LNV functional on range-truncated matrices.
 
     S and H share the block pattern of range r_sh, L has range r_l (Sec. 2).
@@ -195,6 +195,10 @@ def lnv_energy_grad(pos, cell, r_sh, r_l, S: dict, H: dict, L: dict, grad: bool 
       Tr[KS] = 3 Tr[LSLS] - 2 Tr[LSLSLS] = 3 Tr[XX] - 2 Tr[ZX]
     and each gradient term is one masked product onto L's pattern:
       SLH = S Y, HLS = H X, SLSLH = T Y, SLHLS = U X, HLSLS = H Z.
+    With grad_ne, the electron count's gradient (the condition N_e = 2 Tr[KS]
+    of Sec. 2 held during the minimisation needs it):
+      dN_e/dL = 2 (3 * 2 SLS - 2 * 3 SLSLS) = 12 (SLS - SLSLS),
+    with SLS = S X and SLSLS = T X, each masked onto L's pattern.
     """
     r_x = r_l + r_sh
     r_t = r_l + 2.0 * r_sh
@@ -225,6 +229,10 @@ def lnv_energy_grad(pos, cell, r_sh, r_l, S: dict, H: dict, L: dict, grad: bool 
         out["G"] = G
         if keep:
             out.update(U=U, slh=slh, hls=hls, slslh=slslh, slhls=slhls, hlsls=hlsls)
+    if grad_ne:
+        sls = mprod(S, X, pat_l)
+        slsls = mprod(T, X, pat_l)
+        out["GN"] = 12.0 * (sls["val"] - slsls["val"])
     if keep:
         out.update(X=X, Y=Y, T=T, Z=Z, pat_x=pat_x, pat_t=pat_t)
         if not grad:

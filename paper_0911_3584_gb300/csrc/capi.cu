@@ -101,7 +101,7 @@ size_t elem_size(lnv_prec p) { return p == LNV_FP64 ? 8 : 4; }
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-    size_t X, Y, Z, T, U, W, Q, rows, total;
+    size_t X, Y, Z, T, U, W, Q, V, rows, total;
 };
 
 WsLayout ws_layout(const lnv_system *s, int with_grad)
@@ -121,6 +121,7 @@ WsLayout ws_layout(const lnv_system *s, int with_grad)
     L.U = with_grad ? take(s->P_t->nnzb * bs) : 0;
     L.W = with_grad ? take(s->P_lu->nnzb * bs) : 0;
     L.Q = with_grad ? take(s->P_l->nnzb * bs) : 0;
+    L.V = take(s->P_l->nnzb * bs);  // S Z for dN_e/dL
     L.rows = take(sizeof(double) * 4 * (size_t)std::max<int64_t>(s->n, 1));
     L.total = off;
     return L;
@@ -453,7 +454,7 @@ lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
         set_error("autotune allocation: %s", cudaGetErrorString(e));
         return LNV_ERR_OOM;
     }
-    lnv_status st = lnv_energy_grad(ctx, sys, S_dev, H_dev, L_dev, out, G, nullptr, 0);
+    lnv_status st = lnv_energy_grad(ctx, sys, S_dev, H_dev, L_dev, out, G, nullptr, nullptr, 0);
     unsigned char *ws = (unsigned char *)sys->own_ws;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (st == LNV_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
@@ -566,7 +567,7 @@ lnv_status lnv_system_stage_ms(lnv_system *sys, double *ms)
 }
 
 lnv_status lnv_energy_grad(lnv_ctx *ctx, lnv_system *sys, const void *S_dev, const void *H_dev,
-                           const void *L_dev, double *out_dev, void *G_dev, void *ws_dev,
+                           const void *L_dev, double *out_dev, void *G_dev, void *GN_dev, void *ws_dev,
                            size_t ws_bytes)
 {
     LNV_TRY(set_dev(ctx));
@@ -590,6 +591,7 @@ lnv_status lnv_energy_grad(lnv_ctx *ctx, lnv_system *sys, const void *S_dev, con
     }
     void *X = ws + wl.X, *Y = ws + wl.Y, *Z = ws + wl.Z, *T = ws + wl.T;
     void *U = grad ? ws + wl.U : nullptr, *W = grad ? ws + wl.W : nullptr, *Q = grad ? ws + wl.Q : nullptr;
+    void *V = ws + wl.V;
     double *rows = (double *)(ws + wl.rows);
     const int nsf = sys->nsf;
     const lnv_prec pr = sys->prec;
@@ -618,12 +620,19 @@ lnv_status lnv_energy_grad(lnv_ctx *ctx, lnv_system *sys, const void *S_dev, con
     if (grad) {
         // a6: Q = H Z (= HLSLS) on R_L;  a5: W = X^T U^T (= SLHLS) on R_L
         LNV_TRY(multiply(ctx, sys->pl_q, nsf, pr, H_dev, Z, Q));
+        // V = S Z (= SLSLS) on R_L has the patterns of Q = H Z
+        if (GN_dev) LNV_TRY(multiply(ctx, sys->pl_q, nsf, pr, S_dev, Z, V));
         LNV_TRY(mark(5));
         LNV_TRY(multiply(ctx, sys->pl_w, nsf, pr, X, U, W));
         LNV_TRY(mark(6));
         // a7: G = 6(U + U^T) - 4(Q^T + W + Q) on L's pattern
         LNV_TRY(grad_assemble(ctx, sys->P_l, sys->sub_lt, sys->w_map, nsf, pr, U, W, Q, G_dev));
+        if (GN_dev) LNV_TRY(grad_ne_assemble(ctx, sys->P_l, sys->sub_lt, nsf, pr, T, V, GN_dev));
         LNV_TRY(mark(7));
+    } else if (GN_dev) {
+        // a7 (electron count): dN_e/dL = 12 (SLS - SLSLS) on L's pattern
+        LNV_TRY(multiply(ctx, sys->pl_q, nsf, pr, S_dev, Z, V));
+        LNV_TRY(grad_ne_assemble(ctx, sys->P_l, sys->sub_lt, nsf, pr, T, V, GN_dev));
     }
     return LNV_OK;
 }

@@ -187,5 +187,8 @@ lnv_status lnv_combine(lnv_ctx *ctx, int n_seg, double *out);
 lnv_status grad_assemble(lnv_ctx *ctx, const lnv_pattern *PL, const int64_t *sub_LT,
                          const int64_t *w_map, int nsf, lnv_prec prec, const void *U, const void *W,
                          const void *Q, void *G);
+// dN_e/dL = 12 (T - V) on L's pattern, T = SLS read through sub_LT, V = S Z.
+lnv_status grad_ne_assemble(lnv_ctx *ctx, const lnv_pattern *PL, const int64_t *sub_LT, int nsf,
+                            lnv_prec prec, const void *T, const void *V, void *GN);
 
 }  // namespace lnv

@@ -189,6 +189,24 @@ k_grad(int64_t nnzb, const int64_t *__restrict__ tr, const int32_t *__restrict__
     G[p * BS + r] = (T)(6.0 * u - 4.0 * q);
 }
 
+// dN_e/dL = 12 (SLS - SLSLS) on L's pattern (N_e = 2 Tr[KS] with Eq. 3, every
+// stored entry of L independent, S and L symmetric): T = SLS read through the
+// submap of L's pattern in T's, V = S Z = SLSLS formed on L's pattern.
+template <typename T, int NSF>
+__global__ void __launch_bounds__(256)
+k_grad_ne(int64_t nnzb, const int64_t *__restrict__ sub, const T *__restrict__ Tm, const T *__restrict__ V,
+          T *__restrict__ GN)
+{
+    constexpr int BS = NSF * NSF;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nnzb * BS) return;
+    const int64_t p = e / BS;
+    const int r = (int)(e - p * BS);
+    const int64_t pt = sub[p];
+    const double t = pt >= 0 ? (double)Tm[pt * BS + r] : 0.0;
+    GN[p * BS + r] = (T)(12.0 * (t - (double)V[p * BS + r]));
+}
+
 template <typename T, int NSF>
 lnv_status trace_launch(lnv_ctx *ctx, const lnv_pattern *P, int nterms, const void *const *A,
                         const void *const *B, double *row_part)
@@ -283,6 +301,32 @@ lnv_status reduce_rows(lnv_ctx *ctx, const double *row_part, int64_t n, int nter
 lnv_status lnv_combine(lnv_ctx *ctx, int n_seg, double *out)
 {
     k_combine<<<(n_seg + 127) / 128, 128, 0, ctx->stream>>>(n_seg, out);
+    LNV_LAUNCHED();
+    return LNV_OK;
+}
+
+lnv_status grad_ne_assemble(lnv_ctx *ctx, const lnv_pattern *PL, const int64_t *sub_LT, int nsf,
+                            lnv_prec prec, const void *T, const void *V, void *GN)
+{
+    const int64_t total = PL->nnzb * (int64_t)nsf * nsf;
+    if (total == 0) return LNV_OK;
+    const unsigned grid = (unsigned)((total + 255) / 256);
+#define GN_L(TY, N)                                                                                   \
+    k_grad_ne<TY, N><<<grid, 256, 0, ctx->stream>>>(PL->nnzb, sub_LT, (const TY *)T, (const TY *)V, \
+                                                    (TY *)GN)
+    if (prec != LNV_FP64 && prec != LNV_FP32) {
+        set_error("unknown precision %d", (int)prec);
+        return LNV_ERR_ARG;
+    }
+    const bool f64 = prec == LNV_FP64;
+    switch (nsf) {
+    case 1: if (f64) GN_L(double, 1); else GN_L(float, 1); break;
+    case 2: if (f64) GN_L(double, 2); else GN_L(float, 2); break;
+    case 4: if (f64) GN_L(double, 4); else GN_L(float, 4); break;
+    case 9: if (f64) GN_L(double, 9); else GN_L(float, 9); break;
+    default: set_error("NSF=%d is not built (1, 2, 4, 9 are)", nsf); return LNV_ERR_UNSUPPORTED;
+    }
+#undef GN_L
     LNV_LAUNCHED();
     return LNV_OK;
 }

@@ -64,7 +64,7 @@ def lib():
                 "lnv_system_workspace_size": [P, i32, P],
                 "lnv_system_triples": [P, i32, P],
                 "lnv_system_destroy": [P],
-                "lnv_energy_grad": [P, P, P, P, P, P, P, P, ctypes.c_size_t],
+                "lnv_energy_grad": [P, P, P, P, P, P, P, P, P, ctypes.c_size_t],
                 "lnv_system_profile": [P, i32],
                 "lnv_system_stage_ms": [P, P],
                 "lnv_system_stage_triples": [P, P],
@@ -348,10 +348,13 @@ class System:
         """Algorithmic flops of one evaluation: 2 NSF^3 per contributing block triple."""
         return 2 * self.nsf ** 3 * self.triples(grad)
 
-    def energy_grad(self, S, H, L, grad: bool = True, out=None, G=None, workspace=None):
-        """One evaluation; returns (out [n_seg, 6] FP64 device tensor, G or None).
+    def energy_grad(self, S, H, L, grad: bool = True, out=None, G=None, workspace=None,
+                    grad_ne: bool = False, GN=None):
+        """One evaluation; returns (out [n_seg, 6] FP64 device tensor, G or None),
+        or (out, G or None, GN) with grad_ne.
 
-        out[s] = (E, N_e, Tr[LSLH], Tr[LSLSLH], Tr[LSLS], Tr[LSLSLS]).
+        out[s] = (E, N_e, Tr[LSLH], Tr[LSLSLH], Tr[LSLS], Tr[LSLSLS]); G = dE/dL
+        and GN = dN_e/dL on L's pattern.
         """
         s = _vals(S, self.P_sh, self.nsf, self.prec, "S")
         h = _vals(H, self.P_sh, self.nsf, self.prec, "H")
@@ -361,11 +364,16 @@ class System:
         if grad and G is None:
             G = torch.empty_like(L)
         g = _vals(G, self.P_l, self.nsf, self.prec, "G") if grad else ctypes.c_void_p(None)
+        if grad_ne and GN is None:
+            GN = torch.empty_like(L)
+        gn = _vals(GN, self.P_l, self.nsf, self.prec, "GN") if grad_ne else ctypes.c_void_p(None)
         ws, wsb = ctypes.c_void_p(None), 0
         if workspace is not None:
             ws, wsb = _ptr(workspace), workspace.numel() * workspace.element_size()
-        _check(lib().lnv_energy_grad(self.ctx.h, self.h, s, h, l_, _ptr(out), g, ws, wsb),
+        _check(lib().lnv_energy_grad(self.ctx.h, self.h, s, h, l_, _ptr(out), g, gn, ws, wsb),
                "lnv_energy_grad")
+        if grad_ne:
+            return out, (G if grad else None), GN
         return out, (G if grad else None)
 
     STAGES = ("XY", "TU", "Z", "traces", "Q", "W", "G")

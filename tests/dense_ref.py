@@ -41,5 +41,11 @@ def lnv_dense(S, H, L):
     return E, Ne, G, K
 
 
+def ne_grad_dense(S, L):
+    """dN_e/dL = 12 (SLS - SLSLS) for N_e = 2 Tr[KS], densely."""
+    SLS = S @ L @ S
+    return 12 * (SLS - SLS @ L @ S)
+
+
 def random_blocks(rng, nnz, nsf):
     return rng.standard_normal((nnz, nsf, nsf))

@@ -27,7 +27,8 @@ def to_dev(a, dtype, dev):
 
 
 def oracle_lnv(w, S, H, L, grad=True):
-    return oracle.lnv_energy_grad(w["pos"], w["cell"], w["r_sh"], w["r_l"], S, H, L, grad=grad)
+    return oracle.lnv_energy_grad(w["pos"], w["cell"], w["r_sh"], w["r_l"], S, H, L, grad=grad,
+                                  grad_ne=grad)
 
 
 def rounded(M, dtype):

@@ -190,11 +190,15 @@ def test_trace_matches_oracle(ctx, dtype, nsf):
 # ------------------------------------------------------------------ a1-a7 LNV evaluation
 
 def _gpu_lnv(ctx, w, dtype, grad=True, sysm=None):
+    """One evaluation with dE/dL and dN_e/dL (when grad)."""
     if sysm is None:
         sysm = System(ctx, w["nsf"], PREC[dtype], w["pos"], w["cell"], w["r_sh"], w["r_l"])
     S, H, L = (to_dev(w[k], dtype, ctx.device) for k in ("S", "H", "L"))
-    out, G = sysm.energy_grad(S, H, L, grad=grad)
-    return sysm, out.cpu().numpy(), (G.cpu().numpy() if G is not None else None)
+    if grad:
+        out, G, GN = sysm.energy_grad(S, H, L, grad=True, grad_ne=True)
+        return sysm, out.cpu().numpy(), (G.cpu().numpy(), GN.cpu().numpy())
+    out, _ = sysm.energy_grad(S, H, L, grad=False)
+    return sysm, out.cpu().numpy(), None
 
 
 def _check_lnv(out, G, ref, dtype):
@@ -204,6 +208,9 @@ def _check_lnv(out, G, ref, dtype):
     for k, t in enumerate(ref["traces"]):
         assert abs(out[0, 2 + k] - t) <= ts * max(abs(t), 1e-3)
     if G is not None:
+        if isinstance(G, tuple):
+            G, GN = G
+            assert rel_fro(GN, ref["GN"]) <= tm
         assert rel_fro(G, ref["G"]) <= tm
 
 
@@ -262,22 +269,29 @@ def test_autotuned_system_matches_oracle(ctx, dtype):
 
 def test_energy_only_matches_gradient_run(ctx):
     w, S, H, L = workload(2, 4, 6.6, 8.0, seed=3)
-    sysm, out_g, _ = _gpu_lnv(ctx, w, torch.float64, grad=True)
+    sysm, out_g, (_, GN) = _gpu_lnv(ctx, w, torch.float64, grad=True)
     _, out_e, G = _gpu_lnv(ctx, w, torch.float64, grad=False, sysm=sysm)
     assert G is None
     assert np.array_equal(out_g, out_e)
+    # dN_e/dL alone (no dE/dL) equals the one formed beside the gradient
+    Sd, Hd, Ld = (to_dev(w[k], torch.float64, ctx.device) for k in ("S", "H", "L"))
+    out_n, G_n, GN_n = sysm.energy_grad(Sd, Hd, Ld, grad=False, grad_ne=True)
+    assert G_n is None
+    assert np.array_equal(out_n.cpu().numpy(), out_e) and np.array_equal(GN_n.cpu().numpy(), GN)
 
 
 def test_single_atom_closed_form(ctx):
-    """NSF = 1, one atom: E = 2h(3 l^2 s - 2 l^3 s^2), dE/dl = 2h(6 l s - 6 l^2 s^2)."""
+    """NSF = 1, one atom: E = 2h(3 l^2 s - 2 l^3 s^2), dE/dl = 2h(6 l s - 6 l^2 s^2),
+    dN_e/dl = 2(6 l s^2 - 6 l^2 s^3)."""
     s, h, l = 1.3, -0.7, 0.45
     sysm = System(ctx, 1, "fp64", np.zeros((1, 3)), [10.0, 10.0, 10.0], 3.0, 3.0)
     S, H, L = (torch.tensor([[[v]]], dtype=torch.float64, device=ctx.device) for v in (s, h, l))
-    out, G = sysm.energy_grad(S, H, L)
+    out, G, GN = sysm.energy_grad(S, H, L, grad_ne=True)
     out = out.cpu().numpy()[0]
     assert out[0] == pytest.approx(2 * h * (3 * l * l * s - 2 * l ** 3 * s * s), rel=1e-14)
     assert out[1] == pytest.approx(2 * (3 * l * l * s * s - 2 * l ** 3 * s ** 3), rel=1e-14)
     assert G.item() == pytest.approx(2 * h * (6 * l * s - 6 * l * l * s * s), rel=1e-14)
+    assert GN.item() == pytest.approx(2 * (6 * l * s * s - 6 * l * l * s ** 3), rel=1e-14)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -288,8 +302,9 @@ def test_deterministic_and_external_workspace(ctx, dtype):
     assert np.array_equal(out1, out2) and np.array_equal(G1, G2)
     ws = torch.empty(sysm.workspace_size(True), dtype=torch.uint8, device=ctx.device)
     Sd, Hd, Ld = (to_dev(w[k], dtype, ctx.device) for k in ("S", "H", "L"))
-    out3, G3 = sysm.energy_grad(Sd, Hd, Ld, workspace=ws)
-    assert np.array_equal(out3.cpu().numpy(), out1) and np.array_equal(G3.cpu().numpy(), G1)
+    out3, G3, GN3 = sysm.energy_grad(Sd, Hd, Ld, workspace=ws, grad_ne=True)
+    assert np.array_equal(out3.cpu().numpy(), out1) and np.array_equal(G3.cpu().numpy(), G1[0])
+    assert np.array_equal(GN3.cpu().numpy(), G1[1])
 
 
 # ------------------------------------------------------------------ a8 batched systems
@@ -304,13 +319,14 @@ def test_batched_systems_equal_single_runs(ctx, dtype):
     sysb = System(ctx, 4, PREC[dtype], np.concatenate([w["pos"] for w in ws]), [w["cell"] for w in ws],
                   6.6, 8.0, seg_off=off)
     cat = {k: to_dev(np.concatenate([w[k] for w in ws]), dtype, ctx.device) for k in ("S", "H", "L")}
-    out_b, G_b = sysb.energy_grad(cat["S"], cat["H"], cat["L"])
-    out_b, G_b = out_b.cpu().numpy(), G_b.cpu().numpy()
+    out_b, G_b, GN_b = sysb.energy_grad(cat["S"], cat["H"], cat["L"], grad_ne=True)
+    out_b, G_b, GN_b = out_b.cpu().numpy(), G_b.cpu().numpy(), GN_b.cpu().numpy()
     gofs = 0
     for k, w in enumerate(ws):
-        _, out, G = _gpu_lnv(ctx, w, dtype)
+        _, out, (G, GN) = _gpu_lnv(ctx, w, dtype)
         assert np.array_equal(out_b[k], out[0])
         assert np.array_equal(G_b[gofs:gofs + G.shape[0]], G)
+        assert np.array_equal(GN_b[gofs:gofs + G.shape[0]], GN)
         gofs += G.shape[0]
 
 

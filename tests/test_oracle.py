@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import synth
-from tests.dense_ref import from_dense, lnv_dense, mask_dense, to_dense
+from tests.dense_ref import from_dense, lnv_dense, mask_dense, ne_grad_dense, to_dense
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -149,7 +149,7 @@ def test_transpose_and_restrict():
 
 def _check_against_dense(w, S, H, L, rtol=1e-12):
     nsf = w["nsf"]
-    out = oracle.lnv_energy_grad(w["pos"], w["cell"], w["r_sh"], w["r_l"], S, H, L)
+    out = oracle.lnv_energy_grad(w["pos"], w["cell"], w["r_sh"], w["r_l"], S, H, L, grad_ne=True)
     Sd = to_dense(S["rp"], S["col"], S["val"])
     Hd = to_dense(H["rp"], H["col"], H["val"])
     Ld = to_dense(L["rp"], L["col"], L["val"])
@@ -158,6 +158,9 @@ def _check_against_dense(w, S, H, L, rtol=1e-12):
     assert out["Ne"] == pytest.approx(Ne, rel=rtol)
     Gref = from_dense(G, L["rp"], L["col"], nsf)
     err = np.linalg.norm(out["G"] - Gref) / np.linalg.norm(Gref)
+    assert err < rtol
+    GNref = from_dense(ne_grad_dense(Sd, Ld), L["rp"], L["col"], nsf)
+    err = np.linalg.norm(out["GN"] - GNref) / np.linalg.norm(GNref)
     assert err < rtol
     return out
 
@@ -194,24 +197,27 @@ def _dense_system(nsf=4, seed=11):
 @pytest.mark.parametrize("c", [1.0, 0.5, 0.8])
 def test_closed_form_scaled_inverse_overlap(c):
     """L = c S^-1 gives K = (3c^2 - 2c^3) S^-1, N_e = 2 (3c^2 - 2c^3) N NSF,
-    E = 2 (3c^2 - 2c^3) Tr[S^-1 H] and G = 12 (c - c^2) H."""
+    E = 2 (3c^2 - 2c^3) Tr[S^-1 H], G = 12 (c - c^2) H and dN_e/dL =
+    12 (c - c^2) S."""
     w, S, H, L = _dense_system()
     Sd = to_dense(S["rp"], S["col"], S["val"])
     Hd = to_dense(H["rp"], H["col"], H["val"])
     Linv = c * np.linalg.inv(Sd)
     L = oracle.csr(L["rp"], L["col"], from_dense(Linv, L["rp"], L["col"], 4))
-    out = oracle.lnv_energy_grad(w["pos"], w["cell"], 5.0, 5.0, S, H, L)
+    out = oracle.lnv_energy_grad(w["pos"], w["cell"], 5.0, 5.0, S, H, L, grad_ne=True)
     f = 3 * c * c - 2 * c ** 3
     assert out["Ne"] == pytest.approx(2 * f * Sd.shape[0], rel=1e-12)
     assert out["E"] == pytest.approx(2 * f * np.trace(np.linalg.solve(Sd, Hd)), rel=1e-12)
     Gref = from_dense(12 * (c - c * c) * Hd, L["rp"], L["col"], 4)
     assert np.abs(out["G"] - Gref).max() < 1e-12 * max(1.0, np.abs(Hd).max())
+    GNref = from_dense(12 * (c - c * c) * Sd, L["rp"], L["col"], 4)
+    assert np.abs(out["GN"] - GNref).max() < 1e-12 * max(1.0, np.abs(Sd).max())
 
 
 @pytest.mark.parametrize("m", [5, 16])
 def test_closed_form_ground_state_projector(m):
     """L = C C^T from the m lowest generalised eigenvectors of (H, S): K = L,
-    N_e = 2m, E = 2 sum(eps_1..m) and the gradient vanishes."""
+    N_e = 2m, E = 2 sum(eps_1..m), and both gradients vanish."""
     linalg = pytest.importorskip("scipy.linalg")
     w, S, H, L = _dense_system(seed=12)
     Sd = to_dense(S["rp"], S["col"], S["val"])
@@ -220,34 +226,38 @@ def test_closed_form_ground_state_projector(m):
     Cm = C[:, :m]
     Ld = Cm @ Cm.T
     L = oracle.csr(L["rp"], L["col"], from_dense(Ld, L["rp"], L["col"], 4))
-    out = oracle.lnv_energy_grad(w["pos"], w["cell"], 5.0, 5.0, S, H, L)
+    out = oracle.lnv_energy_grad(w["pos"], w["cell"], 5.0, 5.0, S, H, L, grad_ne=True)
     assert out["Ne"] == pytest.approx(2 * m, rel=1e-11)
     assert out["E"] == pytest.approx(2 * eps[:m].sum(), rel=1e-11, abs=1e-11)
     assert np.abs(out["G"]).max() < 1e-11
+    assert np.abs(out["GN"]).max() < 1e-11
 
 
 def test_single_atom_scalar_polynomial():
     """NSF = 1, one atom: E = 2h(3 l^2 s - 2 l^3 s^2), N_e = 2(3 l^2 s^2 - 2 l^3 s^3),
-    dE/dl = 2h(6 l s - 6 l^2 s^2)."""
+    dE/dl = 2h(6 l s - 6 l^2 s^2), dN_e/dl = 2(6 l s^2 - 6 l^2 s^3)."""
     s, h, l = 1.3, -0.7, 0.45
     rp, col = np.array([0, 1]), np.array([0], np.int32)
     S = oracle.csr(rp, col, np.array([[[s]]]))
     H = oracle.csr(rp, col, np.array([[[h]]]))
     L = oracle.csr(rp, col, np.array([[[l]]]))
-    out = oracle.lnv_energy_grad(np.zeros((1, 3)), np.array([10.0, 10.0, 10.0]), 3.0, 3.0, S, H, L)
+    out = oracle.lnv_energy_grad(np.zeros((1, 3)), np.array([10.0, 10.0, 10.0]), 3.0, 3.0, S, H, L,
+                                 grad_ne=True)
     assert out["E"] == pytest.approx(2 * h * (3 * l * l * s - 2 * l ** 3 * s * s), rel=1e-14)
     assert out["Ne"] == pytest.approx(2 * (3 * l * l * s * s - 2 * l ** 3 * s ** 3), rel=1e-14)
     assert out["G"][0, 0, 0] == pytest.approx(2 * h * (6 * l * s - 6 * l * l * s * s), rel=1e-14)
+    assert out["GN"][0, 0, 0] == pytest.approx(2 * (6 * l * s * s - 6 * l * l * s ** 3), rel=1e-14)
 
 
 def test_gradient_against_exact_cubic_differences():
     """E(L + tD) is a cubic in t, so the 4-point Richardson difference
     [8(E(h)-E(-h)) - (E(2h)-E(-2h))] / 12h is exact up to rounding; it must equal
-    <G, D> for symmetric D on L's pattern.  Checked on 20 random blocks."""
+    <G, D> for symmetric D on L's pattern, and the same for N_e and dN_e/dL.
+    Checked on 20 random blocks."""
     w, S, H, L = _si(2, 4, 6.6, 8.0, seed=21)
     rng = np.random.default_rng(99)
-    base = oracle.lnv_energy_grad(w["pos"], w["cell"], 6.6, 8.0, S, H, L)
-    G = base["G"]
+    base = oracle.lnv_energy_grad(w["pos"], w["cell"], 6.6, 8.0, S, H, L, grad_ne=True)
+    G, GN = base["G"], base["GN"]
     rp, col = L["rp"], L["col"]
     n = rp.size - 1
     rows = np.repeat(np.arange(n), np.diff(rp))
@@ -264,14 +274,21 @@ def test_gradient_against_exact_cubic_differences():
         q = np.searchsorted(key, j * n + i)
         D[q] = blk.T
 
-        def e_at(t):
+        def en_at(t):
             Lt = oracle.csr(rp, col, L["val"] + t * D)
-            return oracle.lnv_energy_grad(w["pos"], w["cell"], 6.6, 8.0, S, H, Lt, grad=False)["E"]
+            o = oracle.lnv_energy_grad(w["pos"], w["cell"], 6.6, 8.0, S, H, Lt, grad=False)
+            return o["E"], o["Ne"]
 
-        e = {t: e_at(t * h) for t in (-2, -1, 1, 2)}
+        en = {t: en_at(t * h) for t in (-2, -1, 1, 2)}
+        e = {t: v[0] for t, v in en.items()}
+        ne = {t: v[1] for t, v in en.items()}
         fd = (8 * (e[1] - e[-1]) - (e[2] - e[-2])) / (12 * h)
         an = float((G * D).sum())
         assert fd == pytest.approx(an, rel=1e-8, abs=1e-10)
+        fdn = (8 * (ne[1] - ne[-1]) - (ne[2] - ne[-2])) / (12 * h)
+        # rounding of the four N_e values bounds the difference by about
+        # 18 eps |N_e| / 12h = 3.3e-13 |N_e| at h = 1e-3
+        assert fdn == pytest.approx(float((GN * D).sum()), rel=1e-8, abs=1e-12 * abs(base["Ne"]))
         # five points fix more than a cubic: the cubic through t=-2..2 must
         # also pass through E(0)
         t = np.array([-2.0, -1.0, 1.0, 2.0]) * h
