@@ -197,6 +197,9 @@ lnv_status lnv_system_patterns(const lnv_system *sys, const lnv_pattern **sh,
 /* Device bytes of workspace one evaluation needs (intermediates X, Y, T, U,
  * Z, W, Q and trace partials). */
 lnv_status lnv_system_workspace_size(const lnv_system *sys, int with_grad, size_t *bytes);
+/* Block size, precision and number of independent systems of a system
+ * (any output may be NULL). */
+lnv_status lnv_system_info(const lnv_system *sys, int *nsf, lnv_prec *prec, int *n_seg);
 /* Algorithmic block triples of one evaluation (sum over its products). */
 lnv_status lnv_system_triples(const lnv_system *sys, int with_grad, int64_t *triples);
 /* The same per stage (XY, TU, Z, traces, Q, W, G; 7 values, the TU entry
@@ -242,6 +245,38 @@ lnv_status lnv_system_stage_ms(lnv_system *sys, double *ms7);
 lnv_status lnv_energy_grad(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
                            const void *H_dev, const void *L_dev, double *out_dev,
                            void *G_dev, void *GN_dev, void *ws_dev, size_t ws_bytes);
+
+/* ------------------------------------------------------------------ minimisation
+ * The search for the ground state around the evaluation: vary L on its
+ * pattern to minimise the energy with the electron count set (Sec. 2,
+ * conditions 2 and 3, Eq. 3).  The paper prints no algorithm; lnv_minimize
+ * takes the usual one.  The count is set by a chemical potential mu: the
+ * function minimised is Omega = E - mu N_e = 2 Tr[K (H - mu S)], the band
+ * energy of H - mu S.  Polak-Ribiere conjugate gradients run on L's stored
+ * entries, and each line search is exact: Omega(L + tD) is a cubic in t,
+ * fitted from its value and slope at 0 and two more evaluations.
+ *
+ * Vector kernels on value arrays of n elements in `prec` (device pointers):
+ * out = a x + b y (x or y is not read when its factor is 0; out may alias x
+ * or y), and *out_dev = x . y summed in FP64 in a fixed order (one device
+ * double; uses a scratch buffer the context keeps).  Asynchronous. */
+lnv_status lnv_vec_axpby(lnv_ctx *ctx, lnv_prec prec, int64_t n, double a, const void *x_dev,
+                         double b, const void *y_dev, void *out_dev);
+lnv_status lnv_vec_dot(lnv_ctx *ctx, lnv_prec prec, int64_t n, const void *x_dev, const void *y_dev,
+                       double *out_dev);
+/* Minimise Omega = E - mu N_e over L_dev (updated in place; the system's
+ * precision, L's pattern) for one system (n_seg = 1, else
+ * LNV_ERR_UNSUPPORTED), until the root-mean-square of dOmega/dL is <= tol,
+ * a line search finds no step, or after max_iter iterations.  With mu in a
+ * gap of the spectrum of (H, S) and no truncation the minimum is the
+ * projector on the states below mu.  hist_host (may be NULL) receives up to
+ * max_iter + 1 rows of {Omega, E, N_e, rms of dOmega/dL, previous step
+ * length}; *iters_out the iterations done (rows written = iters + 1).
+ * Allocates five L-sized arrays and one of S's size for the call;
+ * synchronises. */
+lnv_status lnv_minimize(lnv_ctx *ctx, lnv_system *sys, const void *S_dev, const void *H_dev,
+                        void *L_dev, double mu, int max_iter, double tol, double *hist_host,
+                        int *iters_out);
 
 #ifdef __cplusplus
 }

@@ -191,6 +191,7 @@ lnv_status lnv_ctx_set_stream(lnv_ctx *ctx, void *cuda_stream)
 
 lnv_status lnv_ctx_destroy(lnv_ctx *ctx)
 {
+    if (ctx) cudaFree(ctx->scratch);
     delete ctx;
     return LNV_OK;
 }
@@ -386,6 +387,15 @@ lnv_status lnv_system_create(lnv_ctx *ctx, int nsf, lnv_prec prec, const double 
         return LNV_ERR_CUDA;
     }
     *out = s;
+    return LNV_OK;
+}
+
+lnv_status lnv_system_info(const lnv_system *sys, int *nsf, lnv_prec *prec, int *n_seg)
+{
+    LNV_ARG(sys, "null system");
+    if (nsf) *nsf = sys->nsf;
+    if (prec) *prec = sys->prec;
+    if (n_seg) *n_seg = sys->n_seg;
     return LNV_OK;
 }
 

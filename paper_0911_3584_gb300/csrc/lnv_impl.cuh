@@ -63,6 +63,8 @@ struct lnv_ctx {
     cudaStream_t stream;
     int sm_count;
     size_t smem_optin;
+    double *scratch = nullptr;  // reduction partials of lnv_vec_dot (grown on demand)
+    size_t scratch_n = 0;
 };
 
 struct lnv_pattern {
@@ -175,6 +177,14 @@ lnv_status multiply(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec, 
 // Two products sharing A and the patterns of B and C: C1 = A B1, C2 = A B2.
 lnv_status multiply2(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec, const void *A,
                      const void *B1, const void *B2, void *C1, void *C2);
+
+// Vectors on value arrays (minimize.cu): out = a x + b y (x, y not read when
+// their factor is 0); *out_dev = x.y in FP64 (fixed-order reduction)
+lnv_status vec_axpby(lnv_ctx *ctx, lnv_prec prec, int64_t n, double a, const void *x, double b, const void *y,
+                     void *out);
+lnv_status vec_dot(lnv_ctx *ctx, lnv_prec prec, int64_t n, const void *x, const void *y, double *out_dev);
+// out = (x + x^T) / 2 for values on the symmetric block pattern P (out != x)
+lnv_status sym_blocks(lnv_ctx *ctx, lnv_prec prec, const lnv_pattern *P, int nsf, const void *x, void *out);
 
 // Traces and gradient (trace_grad.cu)
 lnv_status trace_rows(lnv_ctx *ctx, const lnv_pattern *P, int nsf, lnv_prec prec, int nterms,

@@ -12,6 +12,7 @@ import ctypes
 import os
 import threading
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -71,6 +72,10 @@ def lib():
                 "lnv_system_stage_kernels": [P, P],
                 "lnv_system_autotune": [P, P, P, P, P, i32, P],
                 "lnv_system_set_stage_kernel": [P, P, i32, i32],
+                "lnv_system_info": [P, P, P, P],
+                "lnv_vec_axpby": [P, i32, i64, dbl, P, dbl, P, P],
+                "lnv_vec_dot": [P, i32, i64, P, P, P],
+                "lnv_minimize": [P, P, P, P, P, dbl, i32, dbl, P, P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -285,6 +290,29 @@ def trace_product(ctx: Context, P: Pattern, A_vals, B_vals, out=None, scratch=No
     return out
 
 
+def vec_axpby(ctx: Context, a: float, x: torch.Tensor, b: float, y: torch.Tensor, out=None) -> torch.Tensor:
+    """out = a x + b y on the device (x, y, out contiguous, same dtype and size)."""
+    prec = FP64 if x.dtype == torch.float64 else FP32
+    if y.dtype != x.dtype or y.numel() != x.numel() or not (x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x and y must be contiguous tensors of one dtype and size")
+    if out is None:
+        out = torch.empty_like(x)
+    _check(lib().lnv_vec_axpby(ctx.h, prec, x.numel(), float(a), _ptr(x), float(b), _ptr(y), _ptr(out)),
+           "lnv_vec_axpby")
+    return out
+
+
+def vec_dot(ctx: Context, x: torch.Tensor, y: torch.Tensor, out=None) -> torch.Tensor:
+    """x . y summed in FP64 in a fixed order, as a 1-element device tensor."""
+    prec = FP64 if x.dtype == torch.float64 else FP32
+    if y.dtype != x.dtype or y.numel() != x.numel() or not (x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x and y must be contiguous tensors of one dtype and size")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=ctx.device)
+    _check(lib().lnv_vec_dot(ctx.h, prec, x.numel(), _ptr(x), _ptr(y), _ptr(out)), "lnv_vec_dot")
+    return out
+
+
 def trace_product_noalloc(ctx: Context, P: Pattern, A_vals, B_vals, out=None) -> torch.Tensor:
     """Tr[A B] through lnv_trace_product_noalloc: no device allocation inside
     the library (its per-row sums use a built-in 2 MiB array, at most 262144
@@ -377,6 +405,21 @@ class System:
         return out, (G if grad else None)
 
     STAGES = ("XY", "TU", "Z", "traces", "Q", "W", "G")
+
+    def minimize(self, S, H, L, mu: float, max_iter: int = 200, tol: float = 1e-8):
+        """Minimise Omega = E - mu N_e over L (updated in place) by conjugate
+        gradients with exact cubic line searches.  Returns (iterations, history
+        [iterations + 1, 5] of (Omega, E, N_e, rms of dOmega/dL, previous step))."""
+        if self.n_seg != 1:
+            raise ValueError("minimize takes one system at a time")
+        s = _vals(S, self.P_sh, self.nsf, self.prec, "S")
+        h = _vals(H, self.P_sh, self.nsf, self.prec, "H")
+        l_ = _vals(L, self.P_l, self.nsf, self.prec, "L")
+        hist = np.zeros((int(max_iter) + 1, 5), dtype=np.float64)
+        it = ctypes.c_int(0)
+        _check(lib().lnv_minimize(self.ctx.h, self.h, s, h, l_, float(mu), int(max_iter), float(tol),
+                                  hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it)), "lnv_minimize")
+        return it.value, hist[: it.value + 1]
 
     def capture(self, S, H, L, grad: bool = True, out=None, G=None, workspace=None):
         """Capture one evaluation in a CUDA graph; returns (graph, out, G).

@@ -429,3 +429,100 @@ def test_graph_captured_batched_evaluation(ctx, dtype):
         tol = TOL[dtype][1]
         assert abs(o[0] - ref["E"]) <= tol * abs(ref["E"]) * 4
         assert abs(o[1] - ref["Ne"]) <= tol * abs(ref["Ne"]) * 4
+
+
+# ------------------------------------------------------------------ minimisation (next row)
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("n", [0, 1, 1000, 300001])
+def test_vector_kernels(ctx, dtype, n):
+    from paper_0911_3584_gb300 import vec_axpby, vec_dot
+    rng = np.random.default_rng(n)
+    x64, y64 = rng.standard_normal(n), rng.standard_normal(n)
+    x, y = to_dev(x64, dtype, ctx.device), to_dev(y64, dtype, ctx.device)
+    xr, yr = x.cpu().double().numpy(), y.cpu().double().numpy()
+    a, b = 0.75, -1.3
+    z = vec_axpby(ctx, a, x, b, y).cpu().double().numpy()
+    ref = a * xr + b * yr
+    ulp = np.finfo(np.float64 if dtype == torch.float64 else np.float32).eps
+    assert np.all(np.abs(z - ref) <= 2 * ulp * (np.abs(a * xr) + np.abs(b * yr)) + 1e-300)
+    # y is not read when its factor is 0 (NaN there must not leak)
+    if n:
+        ynan = torch.full_like(y, float("nan"))
+        assert torch.equal(vec_axpby(ctx, 2.0, x, 0.0, ynan), (2.0 * x.double()).to(dtype))
+    d = vec_dot(ctx, x, y).item()
+    assert d == pytest.approx(float(xr @ yr), rel=1e-13, abs=1e-13 * np.sqrt(max(n, 1)))
+    assert vec_dot(ctx, x, y).item() == d  # fixed reduction order
+
+
+def _dense_min_system(ctx, dtype, m):
+    """Untruncated 8-atom system (every range past the box), mu in the gap
+    above the m-th generalised eigenvalue of (H, S), L = S^-1 / 2."""
+    linalg = pytest.importorskip("scipy.linalg")
+    from tests.dense_ref import from_dense, to_dense
+    w, S, H, L = workload(1, 4, 5.0, 5.0, seed=12)
+    Sd = to_dense(S["rp"], S["col"], S["val"])
+    Hd = to_dense(H["rp"], H["col"], H["val"])
+    eps = linalg.eigh(Hd, Sd, eigvals_only=True)
+    mu = 0.5 * (eps[m - 1] + eps[m])
+    L0 = from_dense(0.5 * np.linalg.inv(Sd), L["rp"], L["col"], 4)
+    return w, S, H, oracle.csr(L["rp"], L["col"], L0), eps, mu
+
+
+@pytest.mark.parametrize("m", [5, 16, 24])
+def test_minimisation_reaches_ground_state(ctx, m):
+    """lnv_minimize (FP64) reaches E = 2 sum eps_1..m and N_e = 2m, as the
+    oracle's loop does."""
+    w, S, H, L0, eps, mu = _dense_min_system(ctx, torch.float64, m)
+    sysm = System(ctx, 4, "fp64", w["pos"], w["cell"], 5.0, 5.0)
+    Sd, Hd, Ld = (to_dev(v, torch.float64, ctx.device) for v in (S["val"], H["val"], L0["val"]))
+    iters, hist = sysm.minimize(Sd, Hd, Ld, mu, max_iter=400, tol=1e-8)
+    assert iters < 400
+    E, Ne = hist[-1, 1], hist[-1, 2]
+    assert E == pytest.approx(2 * eps[:m].sum(), rel=1e-10, abs=1e-10)
+    assert Ne == pytest.approx(2 * m, rel=1e-10)
+    assert np.all(np.diff(hist[:, 0]) <= 1e-12 * abs(hist[-1, 0]))
+    # the evaluation of the returned L agrees with the history's last row
+    out, _ = sysm.energy_grad(Sd, Hd, Ld, grad=False)
+    assert out[0, 1].item() == pytest.approx(Ne, rel=1e-12)
+
+
+def test_minimisation_fp32(ctx):
+    """FP32 products: the loop stops at the rounding of Omega, within 1e-5 of
+    the ground-state energy."""
+    m = 16
+    w, S, H, L0, eps, mu = _dense_min_system(ctx, torch.float32, m)
+    sysm = System(ctx, 4, "fp32", w["pos"], w["cell"], 5.0, 5.0)
+    Sd, Hd, Ld = (to_dev(v, torch.float32, ctx.device) for v in (S["val"], H["val"], L0["val"]))
+    _, hist = sysm.minimize(Sd, Hd, Ld, mu, max_iter=400, tol=1e-6)
+    assert hist[-1, 1] == pytest.approx(2 * eps[:m].sum(), rel=1e-5)
+    assert hist[-1, 2] == pytest.approx(2 * m, rel=1e-5)
+
+
+def test_minimisation_truncated_matches_oracle(ctx):
+    """64 atoms with R_L = 4.5 A inside the 10.9 A box: the truncated minimum
+    found on the GPU equals the oracle loop's."""
+    from oracle.minimize import lnv_minimize as oracle_minimize
+    linalg = pytest.importorskip("scipy.linalg")
+    from tests.dense_ref import to_dense
+    w, S, H, L = workload(2, 4, 3.0, 4.5, seed=5)
+    Sd = to_dense(S["rp"], S["col"], S["val"])
+    Hd = to_dense(H["rp"], H["col"], H["val"])
+    eps = linalg.eigh(Hd, Sd, eigvals_only=True)
+    m = 64
+    mu = 0.5 * (eps[m - 1] + eps[m])
+    # start from the diagonal blocks of S^-1 / 2 (inside L's pattern)
+    Sinv = np.linalg.inv(Sd)
+    rows = np.repeat(np.arange(w["pos"].shape[0]), np.diff(L["rp"]))
+    L0 = np.zeros_like(L["val"])
+    for p, (i, j) in enumerate(zip(rows, L["col"])):
+        if i == j:
+            L0[p] = 0.5 * Sinv[4 * i:4 * i + 4, 4 * j:4 * j + 4]
+    Lo, ho = oracle_minimize(w["pos"], w["cell"], 3.0, 4.5, S, H, oracle.csr(L["rp"], L["col"], L0), mu,
+                             max_iter=300, tol=1e-8)
+    sysm = System(ctx, 4, "fp64", w["pos"], w["cell"], 3.0, 4.5)
+    Sg, Hg, Lg = (to_dev(v, torch.float64, ctx.device) for v in (S["val"], H["val"], L0))
+    _, hg = sysm.minimize(Sg, Hg, Lg, mu, max_iter=300, tol=1e-8)
+    assert hg[-1, 0] == pytest.approx(ho[-1, 0], rel=1e-9)
+    assert hg[-1, 2] == pytest.approx(ho[-1, 2], rel=1e-7)
+    assert hg[-1, 0] >= 2 * (eps[:m] - mu).sum() - 1e-9  # truncation cannot beat the exact minimum

@@ -338,3 +338,49 @@ def test_row_subset_products_and_traces_equal_full_ones():
         np.testing.assert_array_equal(part["val"][sl], full["val"][sl])
     t_full, per_row = oracle.trace(full, full, row_part=True)
     assert oracle.trace(full, full, rows=rows) == pytest.approx(per_row[rows].sum(), rel=1e-14)
+
+
+# ---------------------------------------------------------------- minimisation
+
+def _fill_mu(Sd, Hd, m):
+    linalg = pytest.importorskip("scipy.linalg")
+    eps = linalg.eigh(Hd, Sd, eigvals_only=True)
+    return eps, 0.5 * (eps[m - 1] + eps[m])
+
+
+@pytest.mark.parametrize("m", [5, 16, 24])
+def test_minimisation_reaches_ground_state_projector(m):
+    """Untruncated system, mu in the gap above the m-th state: minimising
+    Omega = E - mu N_e from L = S^-1 / 2 reaches the projector on the m lowest
+    generalised eigenvectors of (H, S): E = 2 sum eps_1..m, N_e = 2m, LSL = L,
+    with Omega never rising along the way."""
+    from oracle.minimize import lnv_minimize
+    w, S, H, L = _dense_system(seed=12)
+    Sd = to_dense(S["rp"], S["col"], S["val"])
+    Hd = to_dense(H["rp"], H["col"], H["val"])
+    eps, mu = _fill_mu(Sd, Hd, m)
+    L0 = oracle.csr(L["rp"], L["col"], from_dense(0.5 * np.linalg.inv(Sd), L["rp"], L["col"], 4))
+    Lf, hist = lnv_minimize(w["pos"], w["cell"], 5.0, 5.0, S, H, L0, mu, max_iter=400, tol=1e-9)
+    omega, E, Ne = hist[-1, 0], hist[-1, 1], hist[-1, 2]
+    assert E == pytest.approx(2 * eps[:m].sum(), rel=1e-10, abs=1e-10)
+    assert Ne == pytest.approx(2 * m, rel=1e-10)
+    assert omega == pytest.approx(2 * (eps[:m] - mu).sum(), rel=1e-10)
+    assert np.all(np.diff(hist[:, 0]) <= 1e-12 * abs(omega))
+    Ld = to_dense(Lf["rp"], Lf["col"], Lf["val"])
+    assert np.linalg.norm(Ld @ Sd @ Ld - Ld) <= 1e-6 * np.linalg.norm(Ld)
+
+
+def test_minimisation_single_atom_closed_form():
+    """NSF = 1, one atom: Omega(l) = 2(h - mu s)(3 l^2 s - 2 l^3 s^2) has its
+    minimum at l = 1/s (the occupied state) when h < mu s."""
+    from oracle.minimize import lnv_minimize
+    s, h, mu = 1.3, -0.7, 0.0
+    rp, col = np.array([0, 1]), np.array([0], np.int32)
+    S = oracle.csr(rp, col, np.array([[[s]]]))
+    H = oracle.csr(rp, col, np.array([[[h]]]))
+    L = oracle.csr(rp, col, np.array([[[0.5 / s]]]))
+    Lf, hist = lnv_minimize(np.zeros((1, 3)), np.array([10.0, 10.0, 10.0]), 3.0, 3.0, S, H, L, mu,
+                            max_iter=50, tol=1e-12)
+    assert Lf["val"][0, 0, 0] == pytest.approx(1.0 / s, rel=1e-9)
+    assert hist[-1, 1] == pytest.approx(2 * h / s, rel=1e-12)
+    assert hist[-1, 2] == pytest.approx(2.0, rel=1e-12)
