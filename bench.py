@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="si4096",
                     choices=["si4096", "batch64", "si32768_nsf9", "si32768_autograd", "si4096_minimize",
-                             "si4096_minimize_fp64"],
+                             "si4096_minimize_fp64", "si4096_truncation"],
                     help="si4096: the benchmark workload; the others are the batched, NSF=9 and "
                          "autograd workloads, reported on their own JSON line")
     ap.add_argument("--kernels", default="",
@@ -548,6 +548,47 @@ def run_minimize(args, ctx, prec):
     print(json.dumps(line), flush=True)
 
 
+def run_truncation(args, ctx):
+    """Approximate truncation of the intermediates on the 4096-atom workload
+    (FP32): time per evaluation and errors of E, N_e and G against the exact
+    FP64 evaluation, for X, Y, Z within r_x and T, U within r_t."""
+    import torch
+
+    from paper_0911_3584_gb300 import System
+
+    w, _ = build_inputs(ctx, torch.float64)
+    S64, H64, L64 = (torch.from_numpy(w[k]).to(ctx.device, torch.float64) for k in ("S", "H", "L"))
+    ex = System(ctx, NSF, "fp64", w["pos"], w["cell"], R_SH, R_L)
+    out_x, G_x = ex.energy_grad(S64, H64, L64)
+    E_x, N_x = out_x[0, 0].item(), out_x[0, 1].item()
+    G_x = G_x.double()
+    del ex
+    rows = []
+    S, H, L = (t.float() for t in (S64, H64, L64))
+    for r_x, r_t in [(None, None), (13.5, 19.0), (12.5, 17.0), (11.5, 15.0), (10.5, 13.0)]:
+        sysm = System(ctx, NSF, "fp32", w["pos"], w["cell"], R_SH, R_L, r_x=r_x, r_t=r_t)
+        sysm.autotune(S, H, L, reps=1)
+        t = _flush_timed(ctx, lambda: sysm.energy_grad(S, H, L), args.steps, args.warmup)
+        out, G = sysm.energy_grad(S, H, L)
+        rows.append({"r_x": r_x or R_L + R_SH, "r_t": r_t or R_L + 2 * R_SH,
+                     "ms": round(t * 1e3 / args.steps, 3), "triples": sysm.triples(True),
+                     "E_rel": abs(out[0, 0].item() - E_x) / abs(E_x),
+                     "Ne_rel": abs(out[0, 1].item() - N_x) / abs(N_x),
+                     "G_rel_fro": (torch.linalg.norm(G.double() - G_x) / torch.linalg.norm(G_x)).item()})
+        del sysm
+    n = w["pos"].shape[0]
+    line = {
+        "metric": METRIC, "value": round(n * args.steps / (rows[0]["ms"] * 1e-3 * args.steps), 1),
+        "unit": "atoms/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": rows[0]["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "atoms": n, "note": "value and ms_per_step: exact ranges; "
+                   "truncation rows: errors against the exact FP64 evaluation"},
+        "truncation": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -575,6 +616,8 @@ def main():
             run_batch64(args, ctx)
         elif args.config == "si32768_nsf9":
             run_large(args, ctx, 9, 10.0, False)
+        elif args.config == "si4096_truncation":
+            run_truncation(args, ctx)
         elif args.config == "si4096_minimize":
             run_minimize(args, ctx, "fp32")
         elif args.config == "si4096_minimize_fp64":

@@ -191,6 +191,19 @@ lnv_status lnv_system_create(lnv_ctx *ctx, int nsf, lnv_prec prec, const double 
                              int64_t n_atoms, int n_seg, const int64_t *seg_off_host,
                              const double *cells_host, double r_sh, double r_l,
                              lnv_system **out);
+/* As lnv_system_create, with the intermediates truncated below their exact
+ * ranges (Sec. 2: the matrices' sparsity is an approximation; the paper notes
+ * that carefully constructed sparse-matrix methods make the cost linear):
+ * X = LS, Y = LH and Z = LSLS kept within r_x (exact: r_l + r_sh), T = SLS
+ * and U = SLH within r_t (exact: r_l + 2 r_sh).  r_x <= 0 or r_t <= 0 selects
+ * the exact range; otherwise r_l <= r_x <= r_l + r_sh and r_l <= r_t <=
+ * r_l + 2 r_sh (LNV_ERR_ARG outside).  Every product is still formed exactly
+ * on its truncated pattern, in the same association as the exact plan, so E,
+ * N_e and G become approximations whose error vanishes at the exact ranges. */
+lnv_status lnv_system_create_truncated(lnv_ctx *ctx, int nsf, lnv_prec prec, const double *pos_dev,
+                                       int64_t n_atoms, int n_seg, const int64_t *seg_off_host,
+                                       const double *cells_host, double r_sh, double r_l, double r_x,
+                                       double r_t, lnv_system **out);
 /* Patterns of S/H and of L (borrowed). */
 lnv_status lnv_system_patterns(const lnv_system *sys, const lnv_pattern **sh,
                                const lnv_pattern **l);

@@ -240,6 +240,48 @@ def lnv_energy_grad(pos, cell, r_sh, r_l, S: dict, H: dict, L: dict, grad: bool 
     return out
 
 
+def lnv_energy_grad_truncated(pos, cell, r_sh, r_l, r_x, r_t, S: dict, H: dict, L: dict,
+                              grad: bool = True) -> dict:
+    """E, N_e and G with the intermediates truncated below their exact ranges.
+
+    The paper keeps every matrix sparse by range (Sec. 2) and leaves the
+    ranges of products to "carefully constructed sparse matrix methods".  Here
+    X = LS and Y = LH are kept within r_x, T = SX and U = SY within r_t, and
+    Z = L T^T within r_x; then, as in the exact case,
+      E = 2 (3 Tr[XY] - 2 Tr[ZY]),  N_e = 2 (3 Tr[XX] - 2 Tr[ZX]),
+      G = 6 (U + U^T) - 4 (Q^T + W + Q) on L's pattern, Q = H Z,
+      W = X^T U^T formed for j >= i and mirrored (W_ji = W_ij^T).
+    With r_x = r_l + r_sh and r_t = r_l + 2 r_sh every product is exact and
+    this equals lnv_energy_grad; below them, the association above defines
+    the approximation (T is then not exactly symmetric, so Z uses T^T and W
+    is taken from one triangle, as the exact plan's symmetric forms do).
+    """
+    pat_x = pattern(pos, cell, r_x)
+    pat_t = pattern(pos, cell, r_t)
+    pat_l = (L["rp"], L["col"])
+    X = mprod(L, S, pat_x)
+    Y = mprod(L, H, pat_x)
+    T = mprod(S, X, pat_t)
+    Z = mprod(L, transpose(T), pat_x)
+    t1, t2, n1, n2 = trace(X, Y), trace(Z, Y), trace(X, X), trace(Z, X)
+    out = {"E": 2.0 * (3.0 * t1 - 2.0 * t2), "Ne": 2.0 * (3.0 * n1 - 2.0 * n2), "traces": (t1, t2, n1, n2)}
+    if grad:
+        U = mprod(S, Y, pat_t)
+        Ul = restrict(U, pat_l)
+        Q = mprod(H, Z, pat_l)
+        W = mprod(transpose(X), transpose(U), pat_l)
+        rp, col = pat_l
+        n = rp.size - 1
+        rows = np.repeat(np.arange(n), np.diff(rp))
+        low = col < rows
+        Wv = W["val"].copy()
+        Wt = transpose(W)["val"]
+        Wv[low] = Wt[low]                       # W_ij = W_ji^T below the diagonal
+        G = 6.0 * (Ul["val"] + transpose(Ul)["val"]) - 4.0 * (transpose(Q)["val"] + Wv + Q["val"])
+        out["G"] = G
+    return out
+
+
 def lnv_rows(S: dict, H: dict, L: dict, full: dict, rows) -> float:
     """Every product and trace of one evaluation, restricted to output rows
     ``rows``, with the operands taken from ``full`` (a ``keep=True`` result of

@@ -322,12 +322,25 @@ lnv_status lnv_system_create(lnv_ctx *ctx, int nsf, lnv_prec prec, const double 
                              int64_t n_atoms, int n_seg, const int64_t *seg_off_host,
                              const double *cells_host, double r_sh, double r_l, lnv_system **out)
 {
+    return lnv_system_create_truncated(ctx, nsf, prec, pos_dev, n_atoms, n_seg, seg_off_host, cells_host, r_sh,
+                                       r_l, 0.0, 0.0, out);
+}
+
+lnv_status lnv_system_create_truncated(lnv_ctx *ctx, int nsf, lnv_prec prec, const double *pos_dev,
+                                       int64_t n_atoms, int n_seg, const int64_t *seg_off_host,
+                                       const double *cells_host, double r_sh, double r_l, double r_x,
+                                       double r_t, lnv_system **out)
+{
     LNV_TRY(set_dev(ctx));
     LNV_ARG(out && pos_dev && cells_host, "null pointer");
     LNV_ARG(nsf == 1 || nsf == 2 || nsf == 4 || nsf == 9, "NSF must be 1, 2, 4 or 9");
     LNV_ARG(prec == LNV_FP64 || prec == LNV_FP32, "unknown precision");
     LNV_ARG(n_seg >= 1, "n_seg < 1");
     LNV_ARG(r_sh > 0 && r_l > 0, "ranges must be positive");
+    if (r_x <= 0.0) r_x = r_l + r_sh;
+    if (r_t <= 0.0) r_t = r_l + 2 * r_sh;
+    LNV_ARG(r_x >= r_l && r_x <= r_l + r_sh, "r_x must lie in [r_l, r_l + r_sh]");
+    LNV_ARG(r_t >= r_l && r_t <= r_l + 2 * r_sh, "r_t must lie in [r_l, r_l + 2 r_sh]");
     std::vector<int64_t> off(n_seg + 1);
     if (n_seg == 1 && !seg_off_host) {
         off[0] = 0;
@@ -356,8 +369,8 @@ lnv_status lnv_system_create(lnv_ctx *ctx, int nsf, lnv_prec prec, const double 
     } while (0)
     SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_sh, &s->P_sh));
     SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_l, &s->P_l));
-    SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_l + r_sh, &s->P_x));
-    SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_l + 2 * r_sh, &s->P_t));
+    SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_x, &s->P_x));
+    SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_t, &s->P_t));
     SYS_TRY(plan_create(ctx, s->P_l, s->P_sh, s->P_x, 0, &s->pl_xy));
     SYS_TRY(plan_create(ctx, s->P_sh, s->P_x, s->P_t, 0, &s->pl_tu));
     // Z = L T: T = SLS is symmetric, so L T = L T^T; the transposed form lets

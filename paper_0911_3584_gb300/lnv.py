@@ -61,6 +61,7 @@ def lib():
                 "lnv_bsr_multiply": [P, P, i32, i32, P, P, P],
                 "lnv_trace_product": [P, P, i32, i32, P, P, P, P],
                 "lnv_system_create": [P, i32, i32, P, i64, i32, P, P, dbl, dbl, PP],
+                "lnv_system_create_truncated": [P, i32, i32, P, i64, i32, P, P, dbl, dbl, dbl, dbl, PP],
                 "lnv_system_patterns": [P, PP, PP],
                 "lnv_system_workspace_size": [P, i32, P],
                 "lnv_system_triples": [P, i32, P],
@@ -335,7 +336,9 @@ class System:
     """One LNV system (or a batch of independent ones): patterns, plans, workspace."""
 
     def __init__(self, ctx: Context, nsf: int, prec, pos, cells, r_sh: float, r_l: float,
-                 seg_off=None):
+                 seg_off=None, r_x: float | None = None, r_t: float | None = None):
+        """r_x, r_t: truncate X, Y, Z to r_x and T, U to r_t (None: the exact
+        ranges r_l + r_sh and r_l + 2 r_sh)."""
         self.ctx, self.nsf, self.prec = ctx, int(nsf), PREC[prec]
         pos = _pos_tensor(pos, ctx.device)
         self.n = pos.shape[0]
@@ -350,9 +353,10 @@ class System:
         off = (ctypes.c_int64 * len(seg_off))(*self.seg_off)
         cv = (ctypes.c_double * len(flat))(*flat)
         h = ctypes.c_void_p()
-        _check(lib().lnv_system_create(ctx.h, self.nsf, self.prec, _ptr(pos), self.n, self.n_seg, off,
-                                       cv, float(r_sh), float(r_l), ctypes.byref(h)),
-               "lnv_system_create")
+        _check(lib().lnv_system_create_truncated(ctx.h, self.nsf, self.prec, _ptr(pos), self.n, self.n_seg,
+                                                 off, cv, float(r_sh), float(r_l), float(r_x or 0.0),
+                                                 float(r_t or 0.0), ctypes.byref(h)),
+               "lnv_system_create_truncated")
         self.h = h
         self.r_sh, self.r_l = float(r_sh), float(r_l)
         sh, l = ctypes.c_void_p(), ctypes.c_void_p()

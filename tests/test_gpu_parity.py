@@ -526,3 +526,26 @@ def test_minimisation_truncated_matches_oracle(ctx):
     assert hg[-1, 0] == pytest.approx(ho[-1, 0], rel=1e-9)
     assert hg[-1, 2] == pytest.approx(ho[-1, 2], rel=1e-7)
     assert hg[-1, 0] >= 2 * (eps[:m] - mu).sum() - 1e-9  # truncation cannot beat the exact minimum
+
+
+# ------------------------------------------------------------------ truncated intermediates (next row)
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("r_x,r_t", [(4.5, 4.5), (5.0, 6.0), (6.0, 8.0), (None, None)])
+def test_truncated_system_matches_oracle(ctx, dtype, r_x, r_t):
+    """512 atoms, R_SH = 3, R_L = 4.5: X, Y, Z kept within r_x and T, U within
+    r_t, against the oracle's definition of the same truncation."""
+    w, S, H, L = workload(4, 4, 3.0, 4.5, seed=6)
+    sysm = System(ctx, 4, PREC[dtype], w["pos"], w["cell"], 3.0, 4.5, r_x=r_x, r_t=r_t)
+    Sd, Hd, Ld = (to_dev(w[k], dtype, ctx.device) for k in ("S", "H", "L"))
+    out, G = sysm.energy_grad(Sd, Hd, Ld)
+    ref = oracle.lnv_energy_grad_truncated(w["pos"], w["cell"], 3.0, 4.5, r_x or 7.5, r_t or 10.5,
+                                           rounded(S, dtype), rounded(H, dtype), rounded(L, dtype))
+    _check_lnv(out.cpu().numpy(), G.cpu().numpy(), ref, dtype)
+
+
+def test_truncation_ranges_are_checked(ctx):
+    w, S, H, L = workload(2, 4, 3.0, 4.5)
+    for r_x, r_t in [(4.0, None), (8.0, None), (None, 4.0), (None, 11.0)]:
+        with pytest.raises(LnvError):
+            System(ctx, 4, "fp64", w["pos"], w["cell"], 3.0, 4.5, r_x=r_x, r_t=r_t)

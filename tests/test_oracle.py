@@ -384,3 +384,32 @@ def test_minimisation_single_atom_closed_form():
     assert Lf["val"][0, 0, 0] == pytest.approx(1.0 / s, rel=1e-9)
     assert hist[-1, 1] == pytest.approx(2 * h / s, rel=1e-12)
     assert hist[-1, 2] == pytest.approx(2.0, rel=1e-12)
+
+
+# ---------------------------------------------------------------- truncated intermediates
+
+def test_truncated_plan_at_exact_ranges_is_the_exact_evaluation():
+    w, S, H, L = _si(2, 4, 6.6, 8.0, seed=4)
+    ex = oracle.lnv_energy_grad(w["pos"], w["cell"], 6.6, 8.0, S, H, L)
+    tr = oracle.lnv_energy_grad_truncated(w["pos"], w["cell"], 6.6, 8.0, 14.6, 21.2, S, H, L)
+    assert tr["E"] == pytest.approx(ex["E"], rel=1e-13)
+    assert tr["Ne"] == pytest.approx(ex["Ne"], rel=1e-13)
+    assert np.linalg.norm(tr["G"] - ex["G"]) <= 1e-12 * np.linalg.norm(ex["G"])
+
+
+def test_truncation_error_shrinks_with_the_ranges():
+    """512 atoms, R_SH = 3, R_L = 4.5 (exact R_X = 7.5, R_T = 10.5 inside the
+    21.7 A box): the errors of E, N_e and G against the exact evaluation fall
+    as the intermediates' ranges grow, and vanish at the exact ranges."""
+    w, S, H, L = _si(4, 4, 3.0, 4.5, seed=6)
+    ex = oracle.lnv_energy_grad(w["pos"], w["cell"], 3.0, 4.5, S, H, L)
+    errs = []
+    for r_x, r_t in [(4.5, 4.5), (5.0, 6.0), (6.0, 8.0), (7.5, 10.5)]:
+        tr = oracle.lnv_energy_grad_truncated(w["pos"], w["cell"], 3.0, 4.5, r_x, r_t, S, H, L)
+        errs.append((abs(tr["E"] - ex["E"]) / abs(ex["E"]), abs(tr["Ne"] - ex["Ne"]) / abs(ex["Ne"]),
+                     np.linalg.norm(tr["G"] - ex["G"]) / np.linalg.norm(ex["G"])))
+    errs = np.array(errs)
+    assert np.all(errs[:-1, 2] > errs[-1, 2])
+    assert np.all(np.diff(errs[:-1, 2]) < 0)
+    assert np.all(errs[-1] < 1e-12)
+    assert errs[0, 2] > 1e-6  # the truncation is really felt
