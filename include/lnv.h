@@ -114,6 +114,15 @@ lnv_status lnv_pattern_info(const lnv_pattern *p, int64_t *n, int64_t *nnzb,
                             const int64_t **row_ptr_dev, const int32_t **col_dev,
                             const int64_t **tr_dev, int *symmetric);
 lnv_status lnv_pattern_destroy(lnv_pattern *p);
+/* Carry block values from one pattern onto another of the same atoms (e.g.
+ * L of an earlier geometry onto the pattern of the next one, to start the
+ * next minimisation from it): block (i, j) of `to` takes block (i, j) of
+ * `from`, zeros where `from` has none.  from_vals_dev and to_vals_dev are
+ * device arrays in `prec` with NSF x NSF blocks; they must not alias.
+ * Asynchronous on the context stream; LNV_ERR_PATTERN if the atom counts
+ * differ. */
+lnv_status lnv_pattern_remap(lnv_ctx *ctx, const lnv_pattern *from, const lnv_pattern *to, int nsf,
+                             lnv_prec prec, const void *from_vals_dev, void *to_vals_dev);
 
 /* ---- a1-a3, a5, a6: masked block products (Sec. 2 operation (i)) ----- */
 

@@ -403,6 +403,17 @@ lnv_status lnv_system_create_truncated(lnv_ctx *ctx, int nsf, lnv_prec prec, con
     return LNV_OK;
 }
 
+lnv_status lnv_pattern_remap(lnv_ctx *ctx, const lnv_pattern *from, const lnv_pattern *to, int nsf,
+                             lnv_prec prec, const void *from_vals_dev, void *to_vals_dev)
+{
+    LNV_TRY(set_dev(ctx));
+    LNV_ARG(from && to && (to->nnzb == 0 || (from_vals_dev && to_vals_dev)), "null pointer");
+    LNV_ARG(nsf == 1 || nsf == 2 || nsf == 4 || nsf == 9, "NSF must be 1, 2, 4 or 9");
+    LNV_ARG(prec == LNV_FP64 || prec == LNV_FP32, "unknown precision");
+    LNV_ARG(from_vals_dev != to_vals_dev || to->nnzb == 0, "the value arrays must not alias");
+    return pattern_remap(ctx, from, to, nsf, prec, from_vals_dev, to_vals_dev);
+}
+
 lnv_status lnv_system_info(const lnv_system *sys, int *nsf, lnv_prec *prec, int *n_seg)
 {
     LNV_ARG(sys, "null system");

@@ -146,6 +146,10 @@ lnv_status pattern_build_impl(lnv_ctx *ctx, const double *pos, int n_seg, const 
                               const double *cells, double cutoff, lnv_pattern **out);
 lnv_status pattern_finish(lnv_ctx *ctx, lnv_pattern *p, bool sort_rows);
 lnv_status pattern_validate(lnv_ctx *ctx, const lnv_pattern *p);
+// Block values carried from one pattern onto another of the same atoms (zeros
+// where `from` has no block).
+lnv_status pattern_remap(lnv_ctx *ctx, const lnv_pattern *from, const lnv_pattern *to, int nsf, lnv_prec prec,
+                         const void *from_vals, void *to_vals);
 void pattern_free(lnv_pattern *p);
 // Upper triangle (col >= row) of P as its own pattern, and for every block
 // (i, j) of P the position of (min(i,j), max(i,j)) in it.

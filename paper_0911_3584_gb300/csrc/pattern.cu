@@ -236,6 +236,20 @@ __global__ void k_submap(const int64_t *__restrict__ s_rp, const int32_t *__rest
     map[p] = find_col(p_col, p_rp[i], p_rp[i + 1], s_col[p]);
 }
 
+// Values of one pattern carried onto another: block (i, j) of `to` takes
+// block (i, j) of `from`, or zeros where `from` has none.
+template <typename T>
+__global__ void k_remap(int64_t nnzb, int bs, const int32_t *__restrict__ t_row, const int32_t *__restrict__ t_col,
+                        const int64_t *__restrict__ f_rp, const int32_t *__restrict__ f_col,
+                        const T *__restrict__ f_val, T *__restrict__ t_val)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= nnzb) return;
+    const int32_t i = t_row[p];
+    const int64_t q = find_col(f_col, f_rp[i], f_rp[i + 1], t_col[p]);
+    for (int e = 0; e < bs; ++e) t_val[p * bs + e] = q >= 0 ? f_val[q * bs + e] : T(0);
+}
+
 // Exclusive scan of int64 counts: out[0..n], out[n] = total.
 __global__ void k_scan_block(const int64_t *__restrict__ in, int64_t n, int64_t *out,
                              int64_t *block_sums)
@@ -535,6 +549,25 @@ lnv_status pattern_submap(lnv_ctx *ctx, const lnv_pattern *sub, const lnv_patter
     if (sub->nnzb == 0) return LNV_OK;
     k_submap<<<(unsigned)((sub->nnzb + 255) / 256), 256, 0, ctx->stream>>>(
         sub->row_ptr, sub->col, sub->row, sub->nnzb, super->row_ptr, super->col, map_dev);
+    LNV_LAUNCHED();
+    return LNV_OK;
+}
+
+lnv_status pattern_remap(lnv_ctx *ctx, const lnv_pattern *from, const lnv_pattern *to, int nsf, lnv_prec prec,
+                         const void *from_vals, void *to_vals)
+{
+    if (from->n != to->n) {
+        set_error("remap between patterns of %lld and %lld atoms", (long long)from->n, (long long)to->n);
+        return LNV_ERR_PATTERN;
+    }
+    if (to->nnzb == 0) return LNV_OK;
+    const unsigned grid = (unsigned)((to->nnzb + 255) / 256);
+    if (prec == LNV_FP64)
+        k_remap<double><<<grid, 256, 0, ctx->stream>>>(to->nnzb, nsf * nsf, to->row, to->col, from->row_ptr,
+                                                       from->col, (const double *)from_vals, (double *)to_vals);
+    else
+        k_remap<float><<<grid, 256, 0, ctx->stream>>>(to->nnzb, nsf * nsf, to->row, to->col, from->row_ptr,
+                                                      from->col, (const float *)from_vals, (float *)to_vals);
     LNV_LAUNCHED();
     return LNV_OK;
 }

@@ -74,6 +74,7 @@ def lib():
                 "lnv_system_autotune": [P, P, P, P, P, i32, P],
                 "lnv_system_set_stage_kernel": [P, P, i32, i32],
                 "lnv_system_info": [P, P, P, P],
+                "lnv_pattern_remap": [P, P, P, i32, i32, P, P],
                 "lnv_vec_axpby": [P, i32, i64, dbl, P, dbl, P, P],
                 "lnv_vec_dot": [P, i32, i64, P, P, P],
                 "lnv_minimize": [P, P, P, P, P, dbl, i32, dbl, P, P],
@@ -219,6 +220,19 @@ class Pattern:
 
     def values(self, nsf: int, dtype=torch.float64) -> torch.Tensor:
         return torch.zeros((self.nnzb, nsf, nsf), dtype=dtype, device=self.ctx.device)
+
+    def remap(self, vals: torch.Tensor, to: "Pattern", out=None) -> torch.Tensor:
+        """Block values on this pattern carried onto `to` (zeros where this
+        pattern has no block), e.g. L of the previous geometry as the start of
+        the next minimisation."""
+        nsf = vals.shape[-1]
+        prec = FP64 if vals.dtype == torch.float64 else FP32
+        v = _vals(vals, self, nsf, prec, "vals")
+        if out is None:
+            out = torch.empty((to.nnzb, nsf, nsf), dtype=vals.dtype, device=self.ctx.device)
+        o = _vals(out, to, nsf, prec, "out")
+        _check(lib().lnv_pattern_remap(self.ctx.h, self.h, to.h, nsf, prec, v, o), "lnv_pattern_remap")
+        return out
 
     def __del__(self):
         if getattr(self, "h", None) and self._owner is None and _lib is not None:

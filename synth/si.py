@@ -122,15 +122,22 @@ def sym_block_values(row_ptr: np.ndarray, col: np.ndarray, pos: np.ndarray,
 
 
 def si_workload(ncell: int, nsf: int, r_sh: float, r_l: float, seed: int, pattern_fn,
-                sigma: float = 0.05):
+                sigma: float = 0.05, displace=None):
     """Positions plus S, H (range r_sh) and L (range r_l) for one Si supercell.
 
     ``pattern_fn(pos, cell, cutoff) -> (row_ptr, col)`` builds the block
     pattern {(i, j): d_ij^2 < cutoff^2}; it is supplied by the caller.
+    ``displace`` (N x 3, Angstrom) moves the atoms after the jitter is drawn
+    and before the values are: with the same seed, values then follow the
+    new distances smoothly wherever the patterns do not change (a step of a
+    geometry optimisation or of molecular dynamics).
     Returns a dict with pos, cell, the two patterns and S, H, L values.
     """
     rng = np.random.default_rng(seed)
     pos, cell = si_diamond_positions(ncell, rng, sigma=sigma)
+    if displace is not None:
+        pos = np.mod(pos + np.asarray(displace, np.float64), cell)
+        pos[pos >= cell] -= cell[np.nonzero(pos >= cell)[1]]
     rp_sh, col_sh = pattern_fn(pos, cell, r_sh)
     rp_l, col_l = pattern_fn(pos, cell, r_l)
     S = sym_block_values(rp_sh, col_sh, pos, cell, nsf, "S", rng)

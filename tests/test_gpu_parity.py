@@ -549,3 +549,76 @@ def test_truncation_ranges_are_checked(ctx):
     for r_x, r_t in [(4.0, None), (8.0, None), (None, 4.0), (None, 11.0)]:
         with pytest.raises(LnvError):
             System(ctx, 4, "fp64", w["pos"], w["cell"], 3.0, 4.5, r_x=r_x, r_t=r_t)
+
+
+# ------------------------------------------------------------------ L carried between geometries (next row)
+
+def _remap_ref(rp_f, col_f, vals, rp_t, col_t):
+    n = len(rp_f) - 1
+    where = {}
+    for i in range(n):
+        for q in range(rp_f[i], rp_f[i + 1]):
+            where[(i, int(col_f[q]))] = q
+    out = np.zeros((len(col_t),) + vals.shape[1:], vals.dtype)
+    for i in range(n):
+        for p in range(rp_t[i], rp_t[i + 1]):
+            q = where.get((i, int(col_t[p])))
+            if q is not None:
+                out[p] = vals[q]
+    return out
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("r_from,r_to", [(5.0, 5.0), (5.0, 6.5), (6.5, 4.0)])
+def test_pattern_remap_is_exact(ctx, dtype, r_from, r_to):
+    rng = np.random.default_rng(int(10 * r_from + r_to))
+    pos, cell = synth.si_diamond_positions(2, rng)
+    Pf = Pattern.build(ctx, pos, cell, r_from)
+    Pt = Pattern.build(ctx, pos, cell, r_to)
+    vals = torch.from_numpy(rng.standard_normal((Pf.nnzb, 4, 4))).to(ctx.device, dtype)
+    got = Pf.remap(vals, Pt).cpu().numpy()
+    ref = _remap_ref(Pf.row_ptr.cpu().numpy(), Pf.col.cpu().numpy(), vals.cpu().numpy(),
+                     Pt.row_ptr.cpu().numpy(), Pt.col.cpu().numpy())
+    assert np.array_equal(got, ref)
+
+
+def test_warm_start_after_a_geometry_step(ctx):
+    """Minimise at one geometry, move the atoms by ~0.01 A (L's pattern changes),
+    and start the next minimisation from the previous L carried onto the new
+    pattern: it reaches the cold start's minimum in fewer iterations."""
+    linalg = pytest.importorskip("scipy.linalg")
+    from tests.dense_ref import to_dense
+    d = np.random.default_rng(1).normal(0.0, 0.01, (64, 3))
+    w0 = synth.si_workload(2, 4, 3.0, 4.5, 5, oracle.pattern)
+    w1 = synth.si_workload(2, 4, 3.0, 4.5, 5, oracle.pattern, displace=d)
+    assert not np.array_equal(w0["l_col"], w1["l_col"])
+    Sd = to_dense(w0["sh_row_ptr"], w0["sh_col"], w0["S"])
+    Hd = to_dense(w0["sh_row_ptr"], w0["sh_col"], w0["H"])
+    eps = linalg.eigh(Hd, Sd, eigvals_only=True)
+    mu = 0.5 * (eps[63] + eps[64])
+
+    def cold_start(w, sysm):
+        Sinv = np.linalg.inv(to_dense(w["sh_row_ptr"], w["sh_col"], w["S"]))
+        P = sysm.P_l
+        rows = np.repeat(np.arange(64), np.diff(P.row_ptr.cpu().numpy()))
+        L0 = np.zeros((P.nnzb, 4, 4))
+        for p, (i, j) in enumerate(zip(rows, P.col.cpu().numpy())):
+            if i == j:
+                L0[p] = 0.5 * Sinv[4 * i:4 * i + 4, 4 * j:4 * j + 4]
+        return to_dev(L0, torch.float64, ctx.device)
+
+    s0 = System(ctx, 4, "fp64", w0["pos"], w0["cell"], 3.0, 4.5)
+    S0, H0 = (to_dev(w0[k], torch.float64, ctx.device) for k in ("S", "H"))
+    L0 = cold_start(w0, s0)
+    s0.minimize(S0, H0, L0, mu, max_iter=400, tol=1e-8)
+
+    s1 = System(ctx, 4, "fp64", w1["pos"], w1["cell"], 3.0, 4.5)
+    S1, H1 = (to_dev(w1[k], torch.float64, ctx.device) for k in ("S", "H"))
+    Lc = cold_start(w1, s1)
+    it_cold, h_cold = s1.minimize(S1, H1, Lc, mu, max_iter=400, tol=1e-8)
+    Lw = s0.P_l.remap(L0, s1.P_l)
+    it_warm, h_warm = s1.minimize(S1, H1, Lw, mu, max_iter=400, tol=1e-8)
+    assert h_warm[-1, 0] == pytest.approx(h_cold[-1, 0], rel=1e-9)
+    assert it_warm < it_cold, (it_warm, it_cold)
+    # the carried L starts far closer to the minimum than the cold start
+    assert h_warm[0, 0] - h_warm[-1, 0] < 1e-2 * (h_cold[0, 0] - h_cold[-1, 0])
