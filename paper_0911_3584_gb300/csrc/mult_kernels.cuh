@@ -219,9 +219,9 @@ k_pull(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
 // order), the blocks of B's row k whose column falls in warp w's slice form a
 // contiguous sub-range (B's rows are sorted); the CTA finds all sub-range
 // bounds with parallel binary searches once per staged k-chunk.  Lanes take
-// (block, output row x) tasks of the sub-range: within one k every column j
-// is distinct, so no two lanes touch one accumulator row, and a __syncwarp
-// separates successive k.  Each slot therefore sums its k's in order
+// (block, output row x, product) tasks of the sub-range: within one k every
+// column j is distinct, so no two lanes touch one accumulator row, and a
+// __syncwarp separates successive k.  Each slot therefore sums its k's in order
 // (deterministic) and no CTA-wide barrier is needed inside the k loop.
 template <typename T, int NSF, int NOUT, bool TA, bool TB, int NW>
 __global__ void __launch_bounds__(NW * 32)
@@ -286,11 +286,13 @@ k_push2(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
             const int32_t k = a_k[qq];
             const int64_t rb = b_rp[k];
             const int64_t lo = rb + bnd[qq * (NW + 1) + warp], hi = rb + bnd[qq * (NW + 1) + warp + 1];
-            const int ntask = (int)(hi - lo) * NSF;
+            // tasks (block, row x, product o): the products are separate tasks so
+            // that a k's few blocks fill more of the warp's lanes
+            const int ntask = (int)(hi - lo) * NSF * NOUT;
             const T *as = a_s + (size_t)qq * BS;
             for (int t = lane; t < ntask; t += 32) {
-                const int64_t p = lo + t / NSF;
-                const int x = t % NSF;
+                const int64_t p = lo + t / (NSF * NOUT);
+                const int xo = t % (NSF * NOUT), x = xo / NOUT, o = xo - x * NOUT;
                 const int32_t j = __ldg(b_col + p);
                 // slot of j inside this warp's slice
                 int lo_s = sl0, hi_s = sl1;
@@ -304,9 +306,8 @@ k_push2(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
                 T ax[NSF];
 #pragma unroll
                 for (int z = 0; z < NSF; ++z) ax[z] = as[x * NSF + z];
-#pragma unroll
-                for (int o = 0; o < NOUT; ++o) {
-                    const T *bblk = (o == 0 ? b_val1 : b_val2) + pb * BS;
+                {
+                    const T *bblk = (NOUT == 1 || o == 0 ? b_val1 : b_val2) + pb * BS;
                     T *ar = acc + ((size_t)o * chunk + lo_s) * BS + x * NSF;
                     T r[NSF];
 #pragma unroll
