@@ -453,6 +453,26 @@ def run_batch64(args, ctx):
         "per_system_launches": {"value": round(n_atoms * args.steps / t_sep, 1), "unit": "atoms/s",
                                 "ms_per_step": round(t_sep * 1e3 / args.steps, 4)},
     }
+    if not args.no_cpu_baseline:
+        # the FP64 oracle on a bounded sample of the batch: its systems of at
+        # most 4^3 cells, in order, each evaluated in full
+        import oracle
+        n_s, t_s = 0, 0.0
+        for w, c in zip(ws, counts):
+            if c > 4:
+                continue
+            S_, H_, L_ = (oracle.csr(w[r], w[col], w[k]) for r, col, k in
+                          (("sh_row_ptr", "sh_col", "S"), ("sh_row_ptr", "sh_col", "H"),
+                           ("l_row_ptr", "l_col", "L")))
+            t0 = time.time()
+            oracle.lnv_energy_grad(w["pos"], w["cell"], R_SH, R_L, S_, H_, L_)
+            t_s += time.time() - t0
+            n_s += w["pos"].shape[0]
+        if n_s:
+            line["cpu_baseline"] = {
+                "value": round(n_s / t_s, 3), "unit": "atoms/s", "cores": oracle.num_threads(),
+                "kind": "oracle", "sample": f"full FP64 evaluations of the batch's systems of at most 4^3 cells "
+                                            f"({n_s} atoms, {t_s:.1f} s)"}
     print(json.dumps(line), flush=True)
 
 
@@ -503,6 +523,10 @@ def run_large(args, ctx, nsf, r_l, autograd):
                    "step": "autograd forward + recompute backward" if autograd else "energy + gradient"},
         "gflops": round(flops * args.steps / t / 1e9, 1),
         "stage_kernels": {k: v[0] for k, v in tuned.items()},
+        "cpu_baseline": {"value": None, "kind": "oracle",
+                         "reason": "not run: the FP64 oracle would hold every intermediate of 32768 atoms "
+                                   "on the host (T alone is 85 M blocks) and take tens of minutes; the "
+                                   "4096-atom benchmark line times it in full"},
         "memory": {"library_workspace_bytes": sysm.workspace_size(True),
                    "torch_peak_bytes_during_steps": int(peak), "torch_bytes_before_steps": int(base_alloc)},
     }
