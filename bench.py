@@ -525,8 +525,8 @@ def run_large(args, ctx, nsf, r_l, autograd):
         "stage_kernels": {k: v[0] for k, v in tuned.items()},
         "cpu_baseline": {"value": None, "kind": "oracle",
                          "reason": "not run: the FP64 oracle would hold every intermediate of 32768 atoms "
-                                   "on the host (T alone is 85 M blocks) and take tens of minutes; the "
-                                   "4096-atom benchmark line times it in full"},
+                                   "on the host (T alone is 86 M blocks) and take minutes (NSF=4) to tens "
+                                   "of minutes (NSF=9); the 4096-atom benchmark line times it in full"},
         "memory": {"library_workspace_bytes": sysm.workspace_size(True),
                    "torch_peak_bytes_during_steps": int(peak), "torch_bytes_before_steps": int(base_alloc)},
     }
