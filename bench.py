@@ -53,7 +53,8 @@ def parse():
                          "autograd workloads, reported on their own JSON line")
     ap.add_argument("--kernels", default="",
                     help="pin product kernels instead of autotuning, e.g. "
-                         "fp32:XY=group-sparse,TU=group;fp64:XY=push (as chosen by the autotuner)")
+                         "fp32:XY=group-sparse,TU=group,mirror=0;fp64:XY=push (as chosen by the "
+                         "autotuner; mirror=1 forms T = SLS on its upper triangle and mirrors it)")
     return ap.parse_args()
 
 
@@ -187,7 +188,10 @@ def time_path(ctx, w, prec, steps, warmup, dist, kernels=None):
     t_system = time.time() - t_setup
     if kernels:
         for st, k in kernels.items():
-            sysm.set_stage_kernel(st, k)
+            if st == "mirror":  # T on its upper triangle and mirrored (1) or whole (0)
+                sysm.set_mirror(k == "1")
+            else:
+                sysm.set_stage_kernel(st, k)
         tuned = {st: (k, None) for st, k in sysm.stage_kernels().items()}
     else:
         tuned = sysm.autotune(S, H, L, reps=2)  # setup: kernel choice per product, untimed
@@ -235,6 +239,7 @@ def time_path(ctx, w, prec, steps, warmup, dist, kernels=None):
         "flops_stage": flops_stage, "launches": launches, "wall": (t0, t1),
         "out": out.cpu().numpy()[0].copy(), "G": G.cpu().numpy().copy(),
         "kernels": {k: v[0] for k, v in tuned.items()},
+        "t_mirrored": sysm.mirror,
         "tensors": (S, H, L, out, G, ws),
         "setup": setup,
     }
@@ -703,6 +708,7 @@ def main():
         "gpu_launches": r32["launches"],
         "stage_ms": {k: round(v, 4) for k, v in r32["stage_ms"].items()},
         "stage_kernels": r32["kernels"],
+        "t_mirrored": r32["t_mirrored"],
         "setup": dict(r32["setup"], note="patterns, plans and tables (system_s) and the autotuner "
                                           "(autotune_s), outside the timed steps"),
     }
@@ -715,7 +721,7 @@ def main():
                         "gflops": round(r64["flops"] / (r64["ms_per_step"] * 1e-3) / 1e9, 1),
                         "roofline": roofline(r64), "gpu_launches": r64["launches"],
                         "stage_ms": {k: round(v, 4) for k, v in r64["stage_ms"].items()},
-                        "stage_kernels": r64["kernels"]}
+                        "stage_kernels": r64["kernels"], "t_mirrored": r64["t_mirrored"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, errs, _ = cpu_baseline(w, [r for r in (r32, r64) if r is not None])
         line["cpu_baseline"] = base

@@ -24,7 +24,9 @@
  *    ((dx*dx)+(dy*dy))+(dz*dz) in IEEE FP64 without fused multiply-adds.
  *  - "_dev" pointers are device memory on the context's device; "_host"
  *    pointers are host memory.  Value arrays are caller-owned; patterns,
- *    plans and systems are library-owned opaque handles.
+ *    plans and systems are library-owned opaque handles.  Device value
+ *    arrays start on a 16-byte boundary (as cudaMalloc's do): the kernels
+ *    move blocks in 16-byte pieces.
  *  - Every call is asynchronous on the context's stream unless it says it
  *    synchronises.  Calls that build handles (pattern, plan, system)
  *    allocate device memory and synchronise the stream.
@@ -61,6 +63,7 @@ typedef enum { LNV_FP64 = 0, LNV_FP32 = 1 } lnv_prec;
  * (A^T)_ik = (A_ki)^T, read through the pattern's transpose map. */
 #define LNV_TRANS_A 1
 #define LNV_TRANS_B 2
+#define LNV_SYM_C 4   /* the product is symmetric: form one triangle, mirror the other */
 
 typedef struct lnv_ctx lnv_ctx;
 typedef struct lnv_pattern lnv_pattern;
@@ -128,7 +131,14 @@ lnv_status lnv_pattern_remap(lnv_ctx *ctx, const lnv_pattern *from, const lnv_pa
 
 /* Plan C = mask_C(op(A) op(B)): for each block (i, j) of C's pattern,
  * C_ij = sum_k op(A)_ik op(B)_kj; nothing outside C's pattern is formed.
- * flags: LNV_TRANS_A / LNV_TRANS_B (needs a symmetric pattern).  The plan
+ * flags: LNV_TRANS_A / LNV_TRANS_B (needs a symmetric pattern).
+ * LNV_SYM_C declares the product symmetric (as S L S is for symmetric S and
+ * L; C's pattern must be symmetric, else LNV_ERR_PATTERN): the kernels that
+ * can skip work form only C's blocks with col >= row, and every element below
+ * the diagonal of the full matrix is then set to its mirror element (blocks
+ * (i, j), j < i, to the transpose of block (j, i)), so the result is exactly
+ * symmetric.  The caller vouches for the symmetry: the lower triangle is not
+ * computed.  The plan
  * chooses a row-gather ("push") or output-owner ("pull") kernel from the
  * patterns' symbolic work counts.  The patterns must outlive the plan.
  * Synchronises. */
@@ -222,7 +232,9 @@ lnv_status lnv_system_workspace_size(const lnv_system *sys, int with_grad, size_
 /* Block size, precision and number of independent systems of a system
  * (any output may be NULL). */
 lnv_status lnv_system_info(const lnv_system *sys, int *nsf, lnv_prec *prec, int *n_seg);
-/* Algorithmic block triples of one evaluation (sum over its products). */
+/* Algorithmic block triples of one evaluation (sum over its products).  T =
+ * SLS is symmetric when X is exact (r_x = r_l + r_sh): only the triples of
+ * its upper triangle (col >= row) count, as only those are formed. */
 lnv_status lnv_system_triples(const lnv_system *sys, int with_grad, int64_t *triples);
 /* The same per stage (XY, TU, Z, traces, Q, W, G; 7 values, the TU entry
  * counting both T and U). */
@@ -237,10 +249,21 @@ lnv_status lnv_system_stage_kernels(const lnv_system *sys, int *k7);
  * hand, in the numbering of lnv_plan_info; as lnv_plan_set_kernel. */
 lnv_status lnv_system_set_stage_kernel(lnv_ctx *ctx, lnv_system *sys, int stage, int kernel);
 
+/* T = SLS is symmetric when X is exact (r_x = r_l + r_sh).  Such a system
+ * forms by default only T's upper triangle (col >= row) where the TU kernel
+ * can skip the rest (push, row groups), then mirrors the lower triangle.
+ * on = 0 forms T whole instead (faster when the kernel's cost does not follow
+ * its multiply-adds); on = 1 on a system with truncated X is
+ * LNV_ERR_UNSUPPORTED.  A change rebuilds the TU plan's row-group tables,
+ * whose column order follows the setting (synchronises).  lnv_system_mirror
+ * reports the setting. */
+lnv_status lnv_system_set_mirror(lnv_ctx *ctx, lnv_system *sys, int on);
+lnv_status lnv_system_mirror(const lnv_system *sys, int *on);
+
 /* Autotuner: runs one evaluation on S, H, L, then times every applicable
  * kernel of each product stage (XY, TU, Z, Q, W) on those intermediates
  * (reps launches each, CUDA events on the context stream) and keeps the
- * fastest.  ms_out (5 x LNV_NUM_KERNELS values, may be NULL) receives the
+ * fastest; for TU each kernel with and without the mirror of T.  ms_out (5 x LNV_NUM_KERNELS values, may be NULL) receives the
  * time of every (stage, kernel) pair tried, -1 for kernels that do not
  * apply.  Allocates and synchronises; results do not change beyond rounding
  * order.  Uses the system's own workspace. */
@@ -256,6 +279,11 @@ lnv_status lnv_system_stage_ms(lnv_system *sys, double *ms7);
 
 /* One evaluation (Sec. 2, Eq. 3).  S_dev, H_dev (on the r_sh pattern) and
  * L_dev (on the r_l pattern) are value arrays in the system's precision.
+ * All three are symmetric, as the overlap, the Hamiltonian and the auxiliary
+ * density matrix are: block (j, i) is the transpose of block (i, j).  The
+ * evaluation relies on it (T = SLS is formed on one triangle and mirrored, and
+ * Z = L T is read as L T^T); the results for a non-symmetric L are
+ * undefined.
  * Writes, per system s, out_dev[6 s + 0..5] = {E, N_e, Tr[LSLH],
  * Tr[LSLSLH], Tr[LSLS], Tr[LSLSLS]} (FP64); when G_dev is not NULL, dE/dL
  * = 6(SLH + HLS) - 4(SLSLH + SLHLS + HLSLS) on L's pattern; when GN_dev is

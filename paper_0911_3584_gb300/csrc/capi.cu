@@ -2,7 +2,8 @@
 //
 // An LNV evaluation (Sec. 2, Eq. 3) runs, on the context stream:
 //   X = L S, Y = L H            push product, one kernel for both (shared A = L)
-//   T = S X, U = S Y            push product, one kernel for both (shared A = S)
+//   T = S X, U = S Y            push product, one kernel for both (shared A = S);
+//                               T = SLS is symmetric: its lower triangle is mirrored
 //   Z = L T  masked to R_X      pull product
 //   Tr[XY], Tr[ZY], Tr[XX], Tr[ZX] -> E, N_e   (one fused FP64 trace pass)
 //   Q = H Z  masked to R_L      pull product
@@ -97,6 +98,9 @@ struct lnv_system {
 namespace {
 
 size_t elem_size(lnv_prec p) { return p == LNV_FP64 ? 8 : 4; }
+
+// Device value arrays start on 16-byte boundaries (NULL passes: optional arrays).
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -304,6 +308,7 @@ lnv_status lnv_bsr_multiply(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_pre
                             const void *A_dev, const void *B_dev, void *C_dev)
 {
     LNV_TRY(set_dev(ctx));
+    LNV_ARG(aligned16(A_dev) && aligned16(B_dev) && aligned16(C_dev), "value arrays must be 16-byte aligned");
     return multiply(ctx, plan, nsf, prec, A_dev, B_dev, C_dev);
 }
 
@@ -313,6 +318,7 @@ lnv_status lnv_trace_product(lnv_ctx *ctx, const lnv_pattern *P, int nsf, lnv_pr
 {
     LNV_TRY(set_dev(ctx));
     LNV_ARG(P && A_dev && B_dev && scratch_dev && out_dev, "null pointer");
+    LNV_ARG(aligned16(A_dev) && aligned16(B_dev), "value arrays must be 16-byte aligned");
     const void *A[1] = {A_dev}, *B[1] = {B_dev};
     LNV_TRY(trace_rows(ctx, P, nsf, prec, 1, A, B, scratch_dev));
     return reduce_rows(ctx, scratch_dev, P->n, 1, 1, nullptr, out_dev, 1, 0);
@@ -372,7 +378,9 @@ lnv_status lnv_system_create_truncated(lnv_ctx *ctx, int nsf, lnv_prec prec, con
     SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_x, &s->P_x));
     SYS_TRY(pattern_build_impl(ctx, pos_dev, n_seg, off.data(), cells_host, r_t, &s->P_t));
     SYS_TRY(plan_create(ctx, s->P_l, s->P_sh, s->P_x, 0, &s->pl_xy));
-    SYS_TRY(plan_create(ctx, s->P_sh, s->P_x, s->P_t, 0, &s->pl_tu));
+    // T = SLS is symmetric when X = LS is exact (L symmetric): only its upper
+    // triangle is formed, the lower one mirrored.  With X truncated it is not.
+    SYS_TRY(plan_create(ctx, s->P_sh, s->P_x, s->P_t, r_x >= r_l + r_sh ? LNV_SYM_C : 0, &s->pl_tu));
     // Z = L T: T = SLS is symmetric, so L T = L T^T; the transposed form lets
     // the merge-join pull read T's row j in order instead of through tr.
     SYS_TRY(plan_create(ctx, s->P_l, s->P_t, s->P_x, LNV_TRANS_B, &s->pl_z));
@@ -411,6 +419,7 @@ lnv_status lnv_pattern_remap(lnv_ctx *ctx, const lnv_pattern *from, const lnv_pa
     LNV_ARG(nsf == 1 || nsf == 2 || nsf == 4 || nsf == 9, "NSF must be 1, 2, 4 or 9");
     LNV_ARG(prec == LNV_FP64 || prec == LNV_FP32, "unknown precision");
     LNV_ARG(from_vals_dev != to_vals_dev || to->nnzb == 0, "the value arrays must not alias");
+    LNV_ARG(aligned16(from_vals_dev) && aligned16(to_vals_dev), "value arrays must be 16-byte aligned");
     return pattern_remap(ctx, from, to, nsf, prec, from_vals_dev, to_vals_dev);
 }
 
@@ -441,9 +450,12 @@ lnv_status lnv_system_workspace_size(const lnv_system *sys, int with_grad, size_
 lnv_status lnv_system_triples(const lnv_system *sys, int with_grad, int64_t *triples)
 {
     LNV_ARG(sys && triples, "null pointer");
-    // X, Y (two products), T (and U), Z, then Q and W
-    int64_t t = 2 * sys->pl_xy->triples + sys->pl_tu->triples + sys->pl_z->triples;
-    if (with_grad) t += sys->pl_tu->triples + sys->pl_q->triples + sys->pl_w->triples;
+    // X, Y (two products), T (its upper triangle when the lower one is
+    // mirrored), Z, then U, Q and W
+    const lnv_plan *tu = sys->pl_tu;
+    int64_t t = 2 * sys->pl_xy->triples + (tu->sym1 && tu->split ? tu->triples_up : tu->triples) +
+                sys->pl_z->triples;
+    if (with_grad) t += tu->triples + sys->pl_q->triples + sys->pl_w->triples;
     *triples = t;
     return LNV_OK;
 }
@@ -471,11 +483,30 @@ lnv_status lnv_system_set_stage_kernel(lnv_ctx *ctx, lnv_system *sys, int stage,
     return plan_set_kernel(ctx, pl, kernel);
 }
 
+lnv_status lnv_system_set_mirror(lnv_ctx *ctx, lnv_system *sys, int on)
+{
+    LNV_TRY(set_dev(ctx));
+    LNV_ARG(sys, "null system");
+    if (on && !sys->pl_tu->sym1) {
+        set_error("T is not symmetric on a system with truncated X");
+        return LNV_ERR_UNSUPPORTED;
+    }
+    return plan_set_split(ctx, sys->pl_tu, on);
+}
+
+lnv_status lnv_system_mirror(const lnv_system *sys, int *on)
+{
+    LNV_ARG(sys && on, "null pointer");
+    *on = sys->pl_tu->sym1 && sys->pl_tu->split;
+    return LNV_OK;
+}
+
 lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev, const void *H_dev,
                                const void *L_dev, int reps, double *ms_out)
 {
     LNV_TRY(set_dev(ctx));
     LNV_ARG(sys && S_dev && H_dev && L_dev, "null pointer");
+    LNV_ARG(aligned16(S_dev) && aligned16(H_dev) && aligned16(L_dev), "value arrays must be 16-byte aligned");
     if (reps < 1) reps = 1;
     // one evaluation fills the intermediates the products read
     const WsLayout wl = ws_layout(sys, 1);
@@ -509,41 +540,52 @@ lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
                        {sys->pl_w, X, U, nullptr, W, nullptr}};
     for (int si = 0; si < 5 && st == LNV_OK; ++si) {
         Stage &sg = stages[si];
-        const int orig = sg.pl->mode;
-        int best = orig;
+        const int orig = sg.pl->mode, orig_split = sg.pl->split;
+        int best = orig, best_split = orig_split;
         float best_ms = 1e30f;
         for (int k = 0; k < LNV_NUM_KERNELS; ++k)
             if (ms_out) ms_out[si * LNV_NUM_KERNELS + k] = -1.0;
-        for (int k : {0, 2, 3, 4, 5, 6, 7}) {
-            // per-warp ring kernel: FP32 values, NSF = 4 (elsewhere kernel 5 is kernel 3)
-            if (k == 5 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
-            // tensor-core kernel: FP32 values, NSF = 4 (3xTF32, FP32-level accuracy)
-            if (k == 6 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
-            // listed triples: NSF = 4 (elsewhere kernel 7 is kernel 0)
-            if (k == 7 && sys->nsf != 4) continue;
-            if (plan_set_kernel(ctx, sg.pl, k) != LNV_OK) continue;
-            lnv_status rs = multiply2(ctx, sg.pl, sys->nsf, sys->prec, sg.A, sg.B1, sg.B2, sg.C1, sg.C2);
-            if (rs == LNV_OK && cudaEventRecord(e0, ctx->stream) == cudaSuccess) {
-                for (int r = 0; r < reps && rs == LNV_OK; ++r)
-                    rs = multiply2(ctx, sg.pl, sys->nsf, sys->prec, sg.A, sg.B1, sg.B2, sg.C1, sg.C2);
-                float ms = 0.f;
-                if (rs == LNV_OK && cudaEventRecord(e1, ctx->stream) == cudaSuccess &&
-                    cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
-                    ms /= reps;
-                    if (ms_out) ms_out[si * LNV_NUM_KERNELS + k] = ms;
-                    if (ms < best_ms) {
-                        best_ms = ms;
-                        best = k;
+        // a symmetric first output (T): every kernel with the split (its upper
+        // triangle, then the mirror) and without (formed whole)
+        for (int split = sg.pl->sym1; split >= 0 && st == LNV_OK; --split) {
+            st = plan_set_split(ctx, sg.pl, split);
+            for (int k : {0, 2, 3, 4, 5, 6, 7}) {
+                if (st != LNV_OK) break;
+                // per-warp ring kernel: FP32 values, NSF = 4 (elsewhere kernel 5 is kernel 3)
+                if (k == 5 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
+                // tensor-core kernel: FP32 values, NSF = 4 (3xTF32, FP32-level accuracy)
+                if (k == 6 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
+                // listed triples: NSF = 4 (elsewhere kernel 7 is kernel 0)
+                if (k == 7 && sys->nsf != 4) continue;
+                if (plan_set_kernel(ctx, sg.pl, k) != LNV_OK) continue;
+                lnv_status rs = multiply2(ctx, sg.pl, sys->nsf, sys->prec, sg.A, sg.B1, sg.B2, sg.C1, sg.C2);
+                if (rs == LNV_OK && cudaEventRecord(e0, ctx->stream) == cudaSuccess) {
+                    for (int r = 0; r < reps && rs == LNV_OK; ++r)
+                        rs = multiply2(ctx, sg.pl, sys->nsf, sys->prec, sg.A, sg.B1, sg.B2, sg.C1, sg.C2);
+                    float ms = 0.f;
+                    if (rs == LNV_OK && cudaEventRecord(e1, ctx->stream) == cudaSuccess &&
+                        cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+                        ms /= reps;
+                        if (ms_out) {
+                            double &slot = ms_out[si * LNV_NUM_KERNELS + k];
+                            if (slot < 0 || ms < slot) slot = ms;
+                        }
+                        if (ms < best_ms) {
+                            best_ms = ms;
+                            best = k;
+                            best_split = split;
+                        }
                     }
                 }
-            }
-            if (rs != LNV_OK) {
-                st = rs;
-                break;
+                if (rs != LNV_OK) st = rs;
             }
         }
+        if (st == LNV_OK) st = plan_set_split(ctx, sg.pl, best_split);
         if (st == LNV_OK) st = plan_set_kernel(ctx, sg.pl, best);
-        else plan_set_kernel(ctx, sg.pl, orig);
+        if (st != LNV_OK) {
+            plan_set_split(ctx, sg.pl, orig_split);
+            plan_set_kernel(ctx, sg.pl, orig);
+        }
         if (st == LNV_OK) plan_trim(sg.pl);
     }
     if (e0) cudaEventDestroy(e0);
@@ -558,7 +600,9 @@ lnv_status lnv_system_stage_triples(const lnv_system *sys, int64_t *t7)
 {
     LNV_ARG(sys && t7, "null pointer");
     t7[0] = 2 * sys->pl_xy->triples;  // X and Y
-    t7[1] = 2 * sys->pl_tu->triples;  // T and U (U only with the gradient)
+    // T (its upper triangle when it is mirrored) and U (U only with the gradient)
+    const lnv_plan *tu = sys->pl_tu;
+    t7[1] = (tu->sym1 && tu->split ? tu->triples_up : tu->triples) + tu->triples;
     t7[2] = sys->pl_z->triples;
     t7[3] = 0;
     t7[4] = sys->pl_q->triples;
@@ -606,6 +650,9 @@ lnv_status lnv_energy_grad(lnv_ctx *ctx, lnv_system *sys, const void *S_dev, con
 {
     LNV_TRY(set_dev(ctx));
     LNV_ARG(sys && S_dev && H_dev && L_dev && out_dev, "null pointer");
+    LNV_ARG(aligned16(S_dev) && aligned16(H_dev) && aligned16(L_dev) && aligned16(G_dev) && aligned16(GN_dev) &&
+                aligned16(ws_dev),
+            "value arrays and the workspace must be 16-byte aligned");
     const int grad = G_dev != nullptr;
     const WsLayout wl = ws_layout(sys, grad);
     unsigned char *ws = (unsigned char *)ws_dev;

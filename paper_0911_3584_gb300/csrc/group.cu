@@ -112,6 +112,7 @@ void group_plan_free(GroupPlan *gp)
     cudaFree(gp->j_off); cudaFree(gp->j_list); cudaFree(gp->cpos);
     cudaFree(gp->bidx_off); cudaFree(gp->bidx);
     cudaFree(gp->hoff); cudaFree(gp->hk); cudaFree(gp->hp);
+    cudaFree(gp->jsplit);
     *gp = GroupPlan();
 }
 
@@ -165,6 +166,10 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
         set_error("row-group lists need %zu bytes, over the %zu budget", need, budget_bytes);
         return LNV_ERR_UNSUPPORTED;
     }
+    // symmetric first output: the upper part of J (j >= the group's first row)
+    // comes first, and jsplit[g] (a multiple of 8) is where the rest starts
+    const bool split = pl->sym1 && pl->split;
+    std::vector<int32_t> jsplit(split ? ng : 0);
     std::vector<int32_t> k_list(k_off[ng]), j_list(j_off[ng]);
     std::vector<int32_t> apos((size_t)k_off[ng] * G, -1), cpos((size_t)j_off[ng] * G, -1);
     {
@@ -188,17 +193,22 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
                     }
                     // Order J by the set of the group's rows whose C row holds j (then by
                     // index): consecutive columns then need the same rows, so a kernel
-                    // can skip the rows that no column of a set keeps.
+                    // can skip the rows that no column of a set keeps.  With a split,
+                    // the columns j >= r0 come first.
                     {
                         const int64_t nj_g = nj[g];
                         std::vector<int32_t> key(nj_g), perm(nj_g);
+                        int64_t n_hi = 0;
                         for (int64_t jl = 0; jl < nj_g; ++jl) {
                             int cm = 0;
                             for (int m = 0; m < G; ++m)
                                 if (cpos[(size_t)(j_off[g] + jl) * G + m] >= 0) cm |= 1 << m;
-                            key[jl] = cm;
+                            const bool hi = split && j_list[j_off[g] + jl] >= r0;
+                            n_hi += hi ? 1 : 0;
+                            key[jl] = cm | (hi ? 1 << G : 0);
                             perm[jl] = (int32_t)jl;
                         }
+                        if (split) jsplit[g] = (int32_t)std::min<int64_t>(nj_g, (n_hi + 7) & ~int64_t(7));
                         std::stable_sort(perm.begin(), perm.end(),
                                          [&](int32_t a, int32_t b) { return key[a] > key[b]; });
                         std::vector<int32_t> jl_new(nj_g), cp_new((size_t)nj_g * G);
@@ -222,8 +232,14 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
     gp.max_k = max_k;
     gp.max_j = max_j;
     gp.candidates = b_off[ng];
+    gp.max_j_hi = gp.max_j_lo = 0;
+    for (int64_t g = 0; g < (int64_t)jsplit.size(); ++g) {
+        gp.max_j_hi = std::max<int>(gp.max_j_hi, jsplit[g]);
+        gp.max_j_lo = std::max<int>(gp.max_j_lo, (int)(nj[g] - jsplit[g]));
+    }
     size_t bytes = 0;
     lnv_status s = LNV_OK;
+    if (split) s = upload(jsplit, &gp.jsplit, &bytes);
     if (s == LNV_OK) s = upload(k_off, &gp.k_off, &bytes);
     if (s == LNV_OK) s = upload(k_list, &gp.k_list, &bytes);
     if (s == LNV_OK) s = upload(apos, &gp.apos, &bytes);

@@ -103,6 +103,11 @@ struct GroupPlan {
     int32_t *hp = nullptr;       // [hits] block index of op(B)_kj's stored block
     int64_t hits = 0, candidates = 0;
     int max_k = 0, max_j = 0;
+    // plans whose first output is symmetric: J lists first the columns j >= the
+    // group's first row (the upper part, padded with lower columns to a
+    // multiple of 8), then the rest; jsplit[g] is where the rest starts
+    int32_t *jsplit = nullptr;   // [n_groups] or absent
+    int max_j_hi = 0, max_j_lo = 0;
     size_t bytes = 0;
 };
 
@@ -121,6 +126,10 @@ struct TriplePlan {
 struct lnv_plan {
     const lnv_pattern *A, *B, *C;
     int trans_a, trans_b;
+    // C1 (the first output) is symmetric, on a symmetric pattern; with split,
+    // the kernels that can form only its blocks with col >= row do so and the
+    // rest is mirrored from them (split = 0: C1 is formed whole)
+    int sym1 = 0, split = 0;
     // 0 push (row gather into a shared-memory row accumulator), 1 pull with a
     // binary search per k, 2 pull with a merge-join walk (symmetric B pattern),
     // 3 row groups with a dense position table, 4 row groups with hit lists,
@@ -134,6 +143,7 @@ struct lnv_plan {
     int2 *items64 = nullptr, *items128 = nullptr;
     int64_t n_items64 = 0, n_items128 = 0;
     int64_t triples;     // contributing block triples
+    int64_t triples_up;  // those of C's blocks with col >= row
     int64_t push_scan;   // B blocks a push kernel scans
     int64_t pull_cand;   // (k, j) candidates a pull kernel tests
     int max_a_row, max_c_row;
@@ -160,12 +170,21 @@ lnv_status pattern_submap(lnv_ctx *ctx, const lnv_pattern *sub, const lnv_patter
                           int64_t *map_dev);
 
 // Product internals (mult.cu)
+// flags: LNV_TRANS_A, LNV_TRANS_B, LNV_SYM_C (the first output of the plan's
+// products is symmetric; C's pattern must be symmetric)
 lnv_status plan_create(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
                        const lnv_pattern *C, int flags, lnv_plan **out);
+// The strict lower triangle of a matrix on the symmetric pattern P set from its
+// upper one: vals[p] = vals[tr p]^T for every block p = (i, j), j < i, and the
+// diagonal blocks made symmetric from their upper elements.
+lnv_status mirror_lower(lnv_ctx *ctx, const lnv_pattern *P, int nsf, lnv_prec prec, void *vals);
 void plan_free(lnv_plan *plan);
 // Free the row-group tables the plan's current kernel does not use.
 void plan_trim(lnv_plan *plan);
 lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel);
+// Form a symmetric first output on one triangle (on = 1) or whole (0); the
+// row-group lists, whose column order follows the setting, are rebuilt.
+lnv_status plan_set_split(lnv_ctx *ctx, lnv_plan *pl, int on);
 // Row-group plan (group.cu); returns LNV_ERR_UNSUPPORTED when the table would
 // not fit the budget or a B row is too long for 16-bit offsets.
 lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes, bool dense,

@@ -279,6 +279,8 @@ extern "C" lnv_status lnv_minimize(lnv_ctx *ctx, lnv_system *sys, const void *S_
     LNV_TRY(set_dev(ctx));
     LNV_ARG(ctx && sys && S_dev && H_dev && L_dev && iters_out, "null pointer");
     LNV_ARG(max_iter >= 0 && tol > 0.0, "max_iter < 0 or tol <= 0");
+    LNV_ARG((((uintptr_t)S_dev | (uintptr_t)H_dev | (uintptr_t)L_dev) & 15u) == 0,
+            "value arrays must be 16-byte aligned");
     const lnv_pattern *PSH = nullptr, *PL = nullptr;
     LNV_TRY(lnv_system_patterns(sys, &PSH, &PL));
     int nseg = 0, nsf = 0;

@@ -24,6 +24,7 @@
 // Operand transposes (op = ^T) read block (k, i) through the pattern's
 // transpose map and transpose it in registers.
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 #include <vector>
 
@@ -48,23 +49,92 @@ __global__ void k_symbolic(int64_t n, const int64_t *__restrict__ a_rp,
     const int64_t i = blockIdx.x;
     if (i >= n) return;
     const int64_t cb = c_rp[i], ce = c_rp[i + 1], ab = a_rp[i], ae = a_rp[i + 1];
-    unsigned long long trip = 0, scan = 0;
+    unsigned long long trip = 0, trip_up = 0, scan = 0;
     for (int64_t s = cb + threadIdx.x; s < ce; s += blockDim.x) {
         int32_t j = c_col[s];
+        unsigned long long t = 0;
         for (int64_t q = ab; q < ae; ++q) {
             int32_t k = a_col[q];
             int64_t bb = b_rp[k], be = b_rp[k + 1];
             int64_t p = lower_bound_g(b_col, bb, be, j);
-            if (p < be && b_col[p] == j) ++trip;
+            if (p < be && b_col[p] == j) ++t;
         }
+        trip += t;
+        if (j >= i) trip_up += t;
     }
     if (threadIdx.x == 0)
         for (int64_t q = ab; q < ae; ++q) scan += (unsigned long long)(b_rp[a_col[q] + 1] - b_rp[a_col[q]]);
     atomicAdd(&counts[0], trip);
+    atomicAdd(&counts[3], trip_up);
     if (threadIdx.x == 0) {
         atomicAdd(&counts[1], scan);
         atomicAdd(&counts[2], (unsigned long long)((ae - ab) * (ce - cb)));
     }
+}
+
+// Strict lower triangle of a symmetric-valued matrix from its upper triangle,
+// one thread per block: block p = (i, j) with j < i becomes the transpose of
+// block tr[p] = (j, i), and a diagonal block's elements (a, b), a > b, become
+// its elements (b, a).  Every element read lies on or above the diagonal, and
+// none of those is written.
+template <typename T, int NSF>
+__global__ void k_mirror_lower(int64_t nnzb, const int32_t *__restrict__ row, const int32_t *__restrict__ col,
+                               const int64_t *__restrict__ tr, T *vals)
+{
+    constexpr int BS = NSF * NSF;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnzb; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = __ldg(row + p), j = __ldg(col + p);
+        if (j > i) continue;
+        T *dst = vals + p * BS;
+        if (j == i) {
+#pragma unroll
+            for (int a = 1; a < NSF; ++a)
+#pragma unroll
+                for (int b = 0; b < a; ++b) dst[a * NSF + b] = dst[b * NSF + a];
+            continue;
+        }
+        const T *src = vals + __ldg(tr + p) * BS;
+        T blk[BS];
+        if constexpr (NSF == 4) {
+            // 16-byte loads and stores (blocks start on 64- or 128-byte boundaries)
+            constexpr int V = 16 / sizeof(T);
+            using Vec = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+#pragma unroll
+            for (int e = 0; e < BS; e += V) *reinterpret_cast<Vec *>(blk + e) = *reinterpret_cast<const Vec *>(src + e);
+            T out[BS];
+#pragma unroll
+            for (int a = 0; a < NSF; ++a)
+#pragma unroll
+                for (int b = 0; b < NSF; ++b) out[a * NSF + b] = blk[b * NSF + a];
+#pragma unroll
+            for (int e = 0; e < BS; e += V) *reinterpret_cast<Vec *>(dst + e) = *reinterpret_cast<const Vec *>(out + e);
+        } else {
+#pragma unroll
+            for (int e = 0; e < BS; ++e) blk[e] = src[e];
+#pragma unroll
+            for (int a = 0; a < NSF; ++a)
+#pragma unroll
+                for (int b = 0; b < NSF; ++b) dst[a * NSF + b] = blk[b * NSF + a];
+        }
+    }
+}
+
+template <typename T>
+lnv_status mirror_launch(lnv_ctx *ctx, const lnv_pattern *P, int nsf, T *vals)
+{
+    // one block per thread: as many loads in flight as the pattern has blocks
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(1 << 30, (P->nnzb + 255) / 256));
+    switch (nsf) {
+    case 1: k_mirror_lower<T, 1><<<grid, 256, 0, ctx->stream>>>(P->nnzb, P->row, P->col, P->tr, vals); break;
+    case 2: k_mirror_lower<T, 2><<<grid, 256, 0, ctx->stream>>>(P->nnzb, P->row, P->col, P->tr, vals); break;
+    case 4: k_mirror_lower<T, 4><<<grid, 256, 0, ctx->stream>>>(P->nnzb, P->row, P->col, P->tr, vals); break;
+    case 9: k_mirror_lower<T, 9><<<grid, 256, 0, ctx->stream>>>(P->nnzb, P->row, P->col, P->tr, vals); break;
+    default:
+        set_error("NSF=%d is not built (1, 2, 4, 9 are)", nsf);
+        return LNV_ERR_UNSUPPORTED;
+    }
+    LNV_LAUNCHED();
+    return LNV_OK;
 }
 
 template <typename T>
@@ -90,7 +160,12 @@ lnv_status plan_create(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
                        const lnv_pattern *C, int flags, lnv_plan **out)
 {
     LNV_ARG(ctx && A && B && C && out, "null pointer");
-    LNV_ARG((flags & ~(LNV_TRANS_A | LNV_TRANS_B)) == 0, "unknown flags");
+    LNV_ARG((flags & ~(LNV_TRANS_A | LNV_TRANS_B | LNV_SYM_C)) == 0, "unknown flags");
+    const int sym1 = (flags & LNV_SYM_C) != 0;
+    if (sym1 && (!C->symmetric || !C->tr)) {
+        set_error("a symmetric output needs a symmetric pattern");
+        return LNV_ERR_PATTERN;
+    }
     if (A->n != B->n || A->n != C->n) {
         set_error("patterns of a product must have the same number of atoms (%lld, %lld, %lld)",
                   (long long)A->n, (long long)B->n, (long long)C->n);
@@ -104,10 +179,11 @@ lnv_status plan_create(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
     lnv_plan *pl = new lnv_plan();
     pl->A = A; pl->B = B; pl->C = C;
     pl->trans_a = ta; pl->trans_b = tb;
+    pl->sym1 = pl->split = sym1 ? 1 : 0;
     pl->max_a_row = A->max_row;
     pl->max_c_row = C->max_row;
     unsigned long long *d_counts = nullptr;
-    unsigned long long h[3] = {0, 0, 0};
+    unsigned long long h[4] = {0, 0, 0, 0};
     cudaError_t e = cudaMalloc(&d_counts, sizeof(h));
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counts, 0, sizeof(h), ctx->stream);
     if (e == cudaSuccess && C->n > 0) {
@@ -125,6 +201,7 @@ lnv_status plan_create(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
         return LNV_ERR_CUDA;
     }
     pl->triples = (int64_t)h[0];
+    pl->triples_up = (int64_t)h[3];
     pl->push_scan = (int64_t)h[1];
     pl->pull_cand = (int64_t)h[2];
     pl->mode = pl->push_scan <= pl->pull_cand ? 0 : (B->symmetric ? 2 : 1);
@@ -216,6 +293,21 @@ lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
     return LNV_OK;
 }
 
+lnv_status plan_set_split(lnv_ctx *ctx, lnv_plan *pl, int on)
+{
+    on = on && pl->sym1 ? 1 : 0;
+    if (pl->split == on) return LNV_OK;
+    pl->split = on;
+    // the row-group lists order J by the split: rebuild the forms present
+    GroupPlan &gp = pl->grp;
+    if (gp.G == 0) return LNV_OK;
+    const bool dense = gp.bidx != nullptr, sparse = gp.hk != nullptr;
+    group_plan_free(&gp);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+    return group_plan_build(ctx, pl, 4, free_b / 3, dense, sparse);
+}
+
 void plan_trim(lnv_plan *plan)
 {
     if (plan->mode != 7) triple_plan_free(&plan->tri);
@@ -248,21 +340,32 @@ void plan_free(lnv_plan *plan)
 lnv_status multiply(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec, const void *A,
                     const void *B, void *C)
 {
-    LNV_ARG(ctx && plan && A && B && C, "null pointer");
-    if (prec == LNV_FP64) return dispatch_nsf<double>(ctx, plan, nsf, A, B, nullptr, C, nullptr);
-    if (prec == LNV_FP32) return dispatch_nsf<float>(ctx, plan, nsf, A, B, nullptr, C, nullptr);
-    set_error("unknown precision %d", (int)prec);
-    return LNV_ERR_ARG;
+    return multiply2(ctx, plan, nsf, prec, A, B, nullptr, C, nullptr);
+}
+
+lnv_status mirror_lower(lnv_ctx *ctx, const lnv_pattern *P, int nsf, lnv_prec prec, void *vals)
+{
+    const int64_t n = P->nnzb * (int64_t)nsf * nsf;
+    if (n == 0) return LNV_OK;
+    if (!P->symmetric || !P->tr) {
+        set_error("mirroring needs a symmetric pattern");
+        return LNV_ERR_PATTERN;
+    }
+    if (prec == LNV_FP64) return mirror_launch<double>(ctx, P, nsf, (double *)vals);
+    return mirror_launch<float>(ctx, P, nsf, (float *)vals);
 }
 
 lnv_status multiply2(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec, const void *A,
                      const void *B1, const void *B2, void *C1, void *C2)
 {
     LNV_ARG(ctx && plan && A && B1 && C1 && (B2 == nullptr) == (C2 == nullptr), "null pointer");
-    if (prec == LNV_FP64) return dispatch_nsf<double>(ctx, plan, nsf, A, B1, B2, C1, C2);
-    if (prec == LNV_FP32) return dispatch_nsf<float>(ctx, plan, nsf, A, B1, B2, C1, C2);
-    set_error("unknown precision %d", (int)prec);
-    return LNV_ERR_ARG;
+    LNV_ARG(prec == LNV_FP64 || prec == LNV_FP32, "unknown precision");
+    // With a symmetric first output the kernels may skip its lower triangle
+    // (they form it only where that is free); it is mirrored afterwards.
+    if (prec == LNV_FP64) LNV_TRY(dispatch_nsf<double>(ctx, plan, nsf, A, B1, B2, C1, C2));
+    else LNV_TRY(dispatch_nsf<float>(ctx, plan, nsf, A, B1, B2, C1, C2));
+    if (plan->sym1 && plan->split) LNV_TRY(mirror_lower(ctx, plan->C, nsf, prec, C1));
+    return LNV_OK;
 }
 
 }  // namespace lnv

@@ -223,7 +223,7 @@ k_pull(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
 // column j is distinct, so no two lanes touch one accumulator row, and a
 // __syncwarp separates successive k.  Each slot therefore sums its k's in order
 // (deterministic) and no CTA-wide barrier is needed inside the k loop.
-template <typename T, int NSF, int NOUT, bool TA, bool TB, int NW>
+template <typename T, int NSF, int NOUT, bool TA, bool TB, int NW, bool SYM>
 __global__ void __launch_bounds__(NW * 32)
 k_push2(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
         const int64_t *__restrict__ a_tr, const T *__restrict__ a_val,
@@ -234,12 +234,13 @@ k_push2(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
         int chunk, int kchunk)
 {
     constexpr int BS = NSF * NSF;
+    constexpr int NB = NW + 2;  // bounds per k: NW + 1 slice starts, then the diagonal
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *acc = reinterpret_cast<T *>(smem_raw);                      // [NOUT][chunk][BS]
     T *a_s = acc + (size_t)NOUT * chunk * BS;                      // [kchunk][BS]
     int32_t *ccol = reinterpret_cast<int32_t *>(a_s + (size_t)kchunk * BS);  // [chunk]
-    int32_t *bnd = ccol + chunk;                                   // [kchunk][NW + 1]
-    int32_t *a_k = bnd + (size_t)kchunk * (NW + 1);                // [kchunk]
+    int32_t *bnd = ccol + chunk;                                   // [kchunk][NB]
+    int32_t *a_k = bnd + (size_t)kchunk * NB;                      // [kchunk]
 
     const int64_t i = blockIdx.x;
     const int64_t cb = c_rp[i], ce = c_rp[i + 1];
@@ -271,28 +272,44 @@ k_push2(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
         for (int t = threadIdx.x; t < kn; t += blockDim.x) a_k[t] = a_col[k0 + t];
         __syncthreads();
         // sub-range bounds: bnd[qq][w] = first block of B's row k with column >=
-        // the first column of slice w (w = NW: past the chunk's last column)
-        for (int t = threadIdx.x; t < kn * (NW + 1); t += blockDim.x) {
-            const int qq = t / (NW + 1), w = t - qq * (NW + 1);
+        // the first column of slice w (w = NW: past the chunk's last column;
+        // w = NW + 1: column i, the diagonal)
+        constexpr int nbw = SYM ? NB : NB - 1;  // the diagonal only when it is used
+        for (int t = threadIdx.x; t < kn * nbw; t += blockDim.x) {
+            const int qq = t / nbw, w = t - qq * nbw;
             const int32_t k = a_k[qq];
             const int s_w = min(cn, w * per_w);
-            const int32_t jkey = s_w < cn ? ccol[s_w] : ccol[cn - 1] + 1;
+            const int32_t jkey = w == NW + 1 ? (int32_t)i : s_w < cn ? ccol[s_w] : ccol[cn - 1] + 1;
             const int64_t rb = b_rp[k];
-            bnd[t] = (int32_t)(lower_bound_g(b_col, rb, b_rp[k + 1], jkey) - rb);
+            bnd[qq * NB + w] = (int32_t)(lower_bound_g(b_col, rb, b_rp[k + 1], jkey) - rb);
         }
         __syncthreads();
         if (sl0 >= sl1) continue;
         for (int qq = 0; qq < kn; ++qq) {
             const int32_t k = a_k[qq];
             const int64_t rb = b_rp[k];
-            const int64_t lo = rb + bnd[qq * (NW + 1) + warp], hi = rb + bnd[qq * (NW + 1) + warp + 1];
+            const int64_t lo = rb + bnd[qq * NB + warp], hi = rb + bnd[qq * NB + warp + 1];
+            // symmetric first output: its blocks left of the diagonal (j < i) are
+            // not formed; those columns take the second product only, if any
+            const int64_t pm = SYM ? max(lo, min(hi, rb + bnd[qq * NB + NW + 1])) : lo;
             // tasks (block, row x, product o): the products are separate tasks so
             // that a k's few blocks fill more of the warp's lanes
-            const int ntask = (int)(hi - lo) * NSF * NOUT;
+            const int n1 = (SYM && NOUT == 2) ? (int)(pm - lo) * NSF : 0;
+            const int ntask = n1 + (int)(hi - pm) * NSF * NOUT;
             const T *as = a_s + (size_t)qq * BS;
             for (int t = lane; t < ntask; t += 32) {
-                const int64_t p = lo + t / (NSF * NOUT);
-                const int xo = t % (NSF * NOUT), x = xo / NOUT, o = xo - x * NOUT;
+                int64_t p;
+                int x, o;
+                if (t < n1) {
+                    p = lo + t / NSF;
+                    x = t % NSF;
+                    o = NOUT - 1;
+                } else {
+                    const int t2 = t - n1, xo = t2 % (NSF * NOUT);
+                    p = pm + t2 / (NSF * NOUT);
+                    x = xo / NOUT;
+                    o = xo - x * NOUT;
+                }
                 const int32_t j = __ldg(b_col + p);
                 // slot of j inside this warp's slice
                 int lo_s = sl0, hi_s = sl1;
@@ -637,7 +654,8 @@ k_grp(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
       const int32_t *__restrict__ hp, const int64_t *__restrict__ a_tr,
       const T *__restrict__ a_val, const int64_t *__restrict__ b_rp,
       const T *__restrict__ b_val1, const T *__restrict__ b_val2, T *__restrict__ c_val1,
-      T *__restrict__ c_val2, int jc, int kchunk, int64_t n_groups)
+      T *__restrict__ c_val2, int jc, int kchunk, int64_t n_groups, const int32_t *__restrict__ jsplit,
+      int part)
 {
     static_assert(NOUT == 1 || NOUT == 2, "one or two products");
     static_assert(NSF % CW == 0, "CW divides NSF");
@@ -657,12 +675,14 @@ k_grp(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
     const int64_t kb = k_off[g], nk = k_off[g + 1] - kb;
     const int64_t jb = j_off[g], nj = j_off[g + 1] - jb;
     const int64_t nj_pad = (nj + 7) & ~int64_t(7);
-    const int64_t j0 = (int64_t)blockIdx.x * jc;
-    if (j0 >= nj) return;
+    // columns [jlo, jhi) of J: all (part 0), the upper part (1) or the rest (2)
+    const int64_t jlo = part == 2 ? jsplit[g] : 0, jhi = part == 1 ? jsplit[g] : nj;
+    const int64_t j0 = jlo + (int64_t)blockIdx.x * jc;
+    if (j0 >= jhi) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int jg = lane / LPJ, c0 = (lane - jg * LPJ) * CW;
     const int groups_cta = (blockDim.x >> 5) * JPW;
-    const int jcn = (int)min((int64_t)jc, nj - j0);
+    const int jcn = (int)min((int64_t)jc, jhi - j0);
     int col[OPT];
     bool jv[OPT];
     int64_t brj[OPT], ptr[OPT], pend[OPT];
@@ -876,7 +896,7 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
      const int64_t *__restrict__ a_tr, const float *__restrict__ a_val,
      const int64_t *__restrict__ b_rp, const float *__restrict__ b_val1,
      const float *__restrict__ b_val2, float *__restrict__ c_val1, float *__restrict__ c_val2,
-     int64_t n_groups)
+     int64_t n_groups, const int32_t *__restrict__ jsplit, int part)
 {
     using S = GwShape<NOUT, D, TA, TB>;
     constexpr int G = S::G, BS = S::BS, OPT = S::OPT, COLS = S::COLS, KC = S::KC, EW = S::EW;
@@ -894,9 +914,11 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
     const int64_t kb = k_off[g], nk = k_off[g + 1] - kb;
     const int64_t jb = j_off[g], nj = j_off[g + 1] - jb;
     const int64_t nj_pad = (nj + 7) & ~int64_t(7);
-    const int64_t j0 = ((int64_t)blockIdx.x * NW + warp) * COLS;
-    if (j0 >= nj) return;
-    const int jcn = (int)min((int64_t)COLS, nj - j0);
+    // columns [jlo, jhi) of J: all (part 0), the upper part (1) or the rest (2)
+    const int64_t jlo = part == 2 ? jsplit[g] : 0, jhi = part == 1 ? jsplit[g] : nj;
+    const int64_t j0 = jlo + ((int64_t)blockIdx.x * NW + warp) * COLS;
+    if (j0 >= jhi) return;
+    const int jcn = (int)min((int64_t)COLS, jhi - j0);
     const int jg = lane >> 2, r = lane & 3;
     // op(B) = B^T: row start of the stored row j for each of the warp's columns
     if (TB)
@@ -1397,16 +1419,23 @@ inline dim3 group_grid(int64_t n_groups, int64_t max_j, int jc)
     return dim3((unsigned)((max_j + jc - 1) / jc), (unsigned)gy, (unsigned)((n_groups + gy - 1) / gy));
 }
 
+// Columns of J a row-group launch covers: part 0 all of them, 1 the upper part
+// of a split plan, 2 the rest.  The widest group's count sizes the grid.
+inline int group_part_width(const GroupPlan &gp, int part)
+{
+    return part == 0 ? gp.max_j : part == 1 ? gp.max_j_hi : gp.max_j_lo;
+}
+
 template <typename T, int NSF, int G, int NOUT, bool TA, bool TB, bool SPARSE>
 lnv_status launch_grp(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
-                      const void *B2, void *C1, void *C2)
+                      const void *B2, void *C1, void *C2, int part)
 {
     constexpr int BS = NSF * NSF;
     constexpr int CW = group_cw<NSF>();
     constexpr int LPJ = NSF / CW;
     constexpr int OPT = NSF == 4 ? 2 : 1;
     const GroupPlan &gp = pl->grp;
-    if (gp.n_groups == 0 || gp.max_j == 0) return LNV_OK;
+    if (gp.n_groups == 0 || group_part_width(gp, part) == 0) return LNV_OK;
     if (SPARSE ? (!gp.hk && gp.hits > 0) : (!gp.bidx && gp.candidates > 0)) {
         set_error("row-group plan lacks the %s", SPARSE ? "hit lists" : "position table");
         return LNV_ERR_UNSUPPORTED;
@@ -1420,22 +1449,22 @@ lnv_status launch_grp(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const voi
     auto kern = k_grp<T, NSF, G, NOUT, CW, OPT, TA, TB, SPARSE>;
     LNV_CUDA(ensure_smem((const void *)kern, smem));
     LNV_CUDA(prefer_smem((const void *)kern));
-    kern<<<group_grid(gp.n_groups, gp.max_j, jc), kGroupThreads, smem, ctx->stream>>>(
+    kern<<<group_grid(gp.n_groups, group_part_width(gp, part), jc), kGroupThreads, smem, ctx->stream>>>(
         gp.k_off, gp.k_list, gp.apos, gp.j_off, gp.j_list, gp.cpos, gp.bidx_off, gp.bidx, gp.hoff,
         gp.hk, gp.hp, pl->A->tr, (const T *)A, pl->B->row_ptr, (const T *)B1, (const T *)B2,
-        (T *)C1, (T *)C2, jc, kchunk, gp.n_groups);
+        (T *)C1, (T *)C2, jc, kchunk, gp.n_groups, gp.jsplit, part);
     LNV_LAUNCHED();
     return LNV_OK;
 }
 
 template <int NOUT, bool TA, bool TB>
 lnv_status launch_gw(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1, const void *B2,
-                     void *C1, void *C2)
+                     void *C1, void *C2, int part)
 {
     constexpr int D = 4, NW = 2;
     using S = GwShape<NOUT, D, TA, TB>;
     const GroupPlan &gp = pl->grp;
-    if (gp.n_groups == 0 || gp.max_j == 0) return LNV_OK;
+    if (gp.n_groups == 0 || group_part_width(gp, part) == 0) return LNV_OK;
     if (!gp.bidx && gp.candidates > 0) {
         set_error("row-group plan lacks the position table");
         return LNV_ERR_UNSUPPORTED;
@@ -1449,10 +1478,10 @@ lnv_status launch_gw(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void
     auto kern = k_gw<NOUT, D, NW, TA, TB>;
     LNV_CUDA(ensure_smem((const void *)kern, smem));
     LNV_CUDA(prefer_smem((const void *)kern));
-    kern<<<group_grid(gp.n_groups, gp.max_j, NW * S::COLS), NW * 32, smem, ctx->stream>>>(
+    kern<<<group_grid(gp.n_groups, group_part_width(gp, part), NW * S::COLS), NW * 32, smem, ctx->stream>>>(
         gp.k_off, gp.apos, gp.j_off, gp.j_list, gp.cpos, gp.bidx_off, gp.bidx, gp.k_list, pl->A->tr,
         (const float *)A, pl->B->row_ptr, (const float *)B1, (const float *)B2, (float *)C1, (float *)C2,
-        gp.n_groups);
+        gp.n_groups, gp.jsplit, part);
     LNV_LAUNCHED();
     return LNV_OK;
 }
@@ -1499,17 +1528,27 @@ lnv_status launch_tri(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const voi
     return LNV_OK;
 }
 
+// part: the columns of J to form (see group_part_width), or -1 to choose: on a
+// plan whose first output is symmetric (split J), the first output is formed
+// on the upper part only (the second, if any, everywhere); the caller then
+// mirrors the first output's lower triangle.
 template <typename T, int NSF, int NOUT, bool TA, bool TB>
 lnv_status launch_group(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
-                        const void *B2, void *C1, void *C2)
+                        const void *B2, void *C1, void *C2, int part = -1)
 {
+    const bool split = part == -1 && pl->sym1 && pl->split && pl->grp.jsplit;
+    if (part == -1) part = split && NOUT == 1 ? 1 : 0;
     if constexpr (NSF == 4 && sizeof(T) == 4) {
         if (pl->mode == 6) return launch_gmma<NOUT, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
     }
     if constexpr (NSF == 4 && sizeof(T) == 4) {
         if (pl->mode == 5) {
-            if (B2) return launch_gw<2, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
-            return launch_gw<1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr);
+            if (B2 && split && NOUT == 2) {
+                LNV_TRY((launch_gw<2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, 1)));
+                return launch_gw<1, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr, 2);
+            }
+            if (B2) return launch_gw<2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, part);
+            return launch_gw<1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, part);
         }
     }
     if (pl->grp.G != 4) {
@@ -1519,11 +1558,15 @@ lnv_status launch_group(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const v
     // Two fused products need two register accumulators per row; for FP64 and
     // for NSF = 9 that exceeds the register file, so they run one at a time.
     if constexpr (NOUT == 2 && (sizeof(T) == 8 || NSF > 4)) {
-        LNV_TRY((launch_group<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr)));
-        return launch_group<T, NSF, 1, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr);
+        LNV_TRY((launch_group<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, split ? 1 : part)));
+        return launch_group<T, NSF, 1, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr, part);
     } else {
-        if (pl->mode == 4) return launch_grp<T, NSF, 4, NOUT, TA, TB, true>(ctx, pl, A, B1, B2, C1, C2);
-        return launch_grp<T, NSF, 4, NOUT, TA, TB, false>(ctx, pl, A, B1, B2, C1, C2);
+        if (split && NOUT == 2) {
+            LNV_TRY((launch_group<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, 1)));
+            return launch_group<T, NSF, 1, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr, 2);
+        }
+        if (pl->mode == 4) return launch_grp<T, NSF, 4, NOUT, TA, TB, true>(ctx, pl, A, B1, B2, C1, C2, part);
+        return launch_grp<T, NSF, 4, NOUT, TA, TB, false>(ctx, pl, A, B1, B2, C1, C2, part);
     }
 }
 
@@ -1531,7 +1574,7 @@ constexpr int kPush2Warps = 4;
 
 template <typename T, int NSF, int NOUT, bool TA, bool TB>
 lnv_status launch_push2(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
-                        const void *B2, void *C1, void *C2)
+                        const void *B2, void *C1, void *C2, int sym = 0)
 {
     constexpr int BS = NSF * NSF;
     constexpr int NW = kPush2Warps;
@@ -1544,8 +1587,8 @@ lnv_status launch_push2(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const v
     int kchunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(PA->max_row, 1),
                                                             (16 * 1024) / (BS * sizeof(T))));
     size_t smem = (size_t)NOUT * chunk * BS * sizeof(T) + (size_t)kchunk * BS * sizeof(T) +
-                  sizeof(int32_t) * ((size_t)chunk + (size_t)kchunk * (NW + 1) + kchunk) + 16;
-    auto kern = k_push2<T, NSF, NOUT, TA, TB, NW>;
+                  sizeof(int32_t) * ((size_t)chunk + (size_t)kchunk * (NW + 2) + kchunk) + 16;
+    auto kern = sym ? k_push2<T, NSF, NOUT, TA, TB, NW, true> : k_push2<T, NSF, NOUT, TA, TB, NW, false>;
     LNV_CUDA(ensure_smem((const void *)kern, smem));
     dim3 grid((unsigned)PC->n, (unsigned)((PC->max_row + chunk - 1) / chunk));
     kern<<<grid, NW * 32, smem, ctx->stream>>>(
@@ -1599,8 +1642,8 @@ lnv_status dispatch_mode(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const 
             return LNV_OK;
         } else {
             // other block sizes: the push kernel, which needs no tables
-            if (B2) return launch_push2<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
-            return launch_push2<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr);
+            if (B2) return launch_push2<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, pl->sym1 && pl->split);
+            return launch_push2<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, pl->sym1 && pl->split);
         }
     }
     if (pl->mode >= 3) {
@@ -1613,8 +1656,8 @@ lnv_status dispatch_mode(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const 
         return LNV_OK;
     }
     if (pl->mode == 0) {
-        if (B2) return launch_push2<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
-        return launch_push2<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr);
+        if (B2) return launch_push2<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, pl->sym1 && pl->split);
+        return launch_push2<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, pl->sym1 && pl->split);
     }
     LNV_TRY((launch_pull<T, NSF, TA, TB>(ctx, pl, A, B1, C1)));
     if (B2) LNV_TRY((launch_pull<T, NSF, TA, TB>(ctx, pl, A, B2, C2)));

@@ -60,6 +60,7 @@ extern "C" lnv_status lnv_trace_product_noalloc(lnv_ctx *ctx, const lnv_pattern 
                                                 const void *B_dev, double *out_dev)
 {
     LNV_ARG(ctx && P && A_dev && B_dev && out_dev, "null pointer");
+    LNV_ARG((((uintptr_t)A_dev | (uintptr_t)B_dev) & 15u) == 0, "value arrays must be 16-byte aligned");
     if (P->n > kNoAllocMaxRows) {
         lnv::set_error("lnv_trace_product_noalloc: pattern has %lld rows, the built-in scratch "
                        "holds at most %lld; use lnv_trace_product with caller scratch",

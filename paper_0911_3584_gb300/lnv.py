@@ -23,7 +23,7 @@ _lock = threading.Lock()
 FP64, FP32 = 0, 1
 PREC = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
 DTYPE = {FP64: torch.float64, FP32: torch.float32}
-TRANS_A, TRANS_B = 1, 2
+TRANS_A, TRANS_B, SYM_C = 1, 2, 4
 
 
 class LnvError(RuntimeError):
@@ -73,6 +73,8 @@ def lib():
                 "lnv_system_stage_kernels": [P, P],
                 "lnv_system_autotune": [P, P, P, P, P, i32, P],
                 "lnv_system_set_stage_kernel": [P, P, i32, i32],
+                "lnv_system_set_mirror": [P, P, i32],
+                "lnv_system_mirror": [P, P],
                 "lnv_system_info": [P, P, P, P],
                 "lnv_pattern_remap": [P, P, P, i32, i32, P, P],
                 "lnv_vec_axpby": [P, i32, i64, dbl, P, dbl, P, P],
@@ -256,9 +258,12 @@ def _vals(t: torch.Tensor, pattern: Pattern, nsf: int, prec: int, name: str):
 class Plan:
     """C = mask_C(op(A) op(B)) on fixed patterns."""
 
-    def __init__(self, ctx: Context, A: Pattern, B: Pattern, C: Pattern, trans_a=False, trans_b=False):
+    def __init__(self, ctx: Context, A: Pattern, B: Pattern, C: Pattern, trans_a=False, trans_b=False,
+                 sym_c=False):
+        """sym_c: the product is symmetric; only its upper triangle is formed and
+        the lower one mirrored (C's pattern must be symmetric)."""
         self.ctx, self.A, self.B, self.C = ctx, A, B, C
-        flags = (TRANS_A if trans_a else 0) | (TRANS_B if trans_b else 0)
+        flags = (TRANS_A if trans_a else 0) | (TRANS_B if trans_b else 0) | (SYM_C if sym_c else 0)
         h = ctypes.c_void_p()
         _check(lib().lnv_plan_product(ctx.h, A.h, B.h, C.h, flags, ctypes.byref(h)), "lnv_plan_product")
         self.h = h
@@ -483,6 +488,17 @@ class System:
         k = Plan.KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)
         _check(lib().lnv_system_set_stage_kernel(self.ctx.h, self.h, self.STAGES.index(stage), k),
                "lnv_system_set_stage_kernel")
+
+    @property
+    def mirror(self) -> bool:
+        """True when T = SLS is formed on its upper triangle and mirrored."""
+        v = ctypes.c_int()
+        _check(lib().lnv_system_mirror(self.h, ctypes.byref(v)), "lnv_system_mirror")
+        return bool(v.value)
+
+    def set_mirror(self, on: bool):
+        """Form T on its upper triangle and mirror it (True), or whole (False)."""
+        _check(lib().lnv_system_set_mirror(self.ctx.h, self.h, int(on)), "lnv_system_set_mirror")
 
     def autotune(self, S, H, L, reps: int = 3) -> dict:
         """Time every applicable kernel per product stage on these inputs and

@@ -133,6 +133,95 @@ def test_masked_product_matches_oracle(ctx, dtype, nsf, case, kernel):
     assert plan.triples > 0
 
 
+@pytest.mark.parametrize("kernel", ["default", "push", "pull", "pull-merge", "group", "group-sparse",
+                                    "group-pipe", "group-mma", "triples"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("nsf", [1, 4, 9])
+def test_symmetric_product_formed_on_one_triangle(ctx, dtype, nsf, kernel):
+    """T = S (L S) with symmetric S, L declared symmetric (LNV_SYM_C): the kernels
+    form its upper triangle (the two-output form too: U = S (L H) alongside) and
+    the lower triangle is mirrored.  Against the oracle's full product; the
+    result is exactly symmetric."""
+    ncell = 2 if nsf == 9 else 3
+    w = synth.si_workload(ncell, nsf, 6.6, 8.0, nsf, oracle.pattern)
+    pos, cell = w["pos"], w["cell"]
+    S = rounded(oracle.csr(w["sh_row_ptr"], w["sh_col"], w["S"]), dtype)
+    H = rounded(oracle.csr(w["sh_row_ptr"], w["sh_col"], w["H"]), dtype)
+    L = rounded(oracle.csr(w["l_row_ptr"], w["l_col"], w["L"]), dtype)
+    ox, ot = oracle.pattern(pos, cell, 14.6), oracle.pattern(pos, cell, 21.2)
+    X = rounded(oracle.mprod(L, S, ox), dtype)
+    Y = rounded(oracle.mprod(L, H, ox), dtype)
+    PS, PX, PT = (Pattern.build(ctx, pos, cell, r) for r in (6.6, 14.6, 21.2))
+    plan = Plan(ctx, PS, PX, PT, sym_c=True)
+    if kernel != "default":
+        plan.set_kernel(kernel)
+    dev = ctx.device
+    T = plan.multiply(to_dev(S["val"], dtype, dev), to_dev(X["val"], dtype, dev)).cpu().numpy()
+    ref_t = oracle.mprod(S, X, ot)["val"]
+    assert rel_fro(T, ref_t) <= TOL[dtype][0], plan.mode
+    tr = PT.tr.cpu().numpy()
+    assert np.array_equal(T, np.swapaxes(T[tr], 1, 2))
+    # the fused pair through a system-style two-output call: T and U together
+    sysm = System(ctx, nsf, PREC[dtype], pos, cell, 6.6, 8.0)
+    if kernel != "default":
+        sysm.set_stage_kernel("TU", kernel)
+    Sd, Hd, Ld = (to_dev(M["val"], dtype, dev) for M in (S, H, L))
+    ref = oracle_lnv(w, S, H, L)
+    assert sysm.mirror
+    for mirror in (True, False):
+        sysm.set_mirror(mirror)
+        out, G = sysm.energy_grad(Sd, Hd, Ld)
+        assert rel_fro(G.cpu().numpy(), ref["G"]) <= TOL[dtype][0], mirror
+        assert abs(out.cpu().numpy()[0][0] - ref["E"]) <= TOL[dtype][1] * abs(ref["E"]), mirror
+        assert abs(out.cpu().numpy()[0][1] - ref["Ne"]) <= TOL[dtype][1] * abs(ref["Ne"]), mirror
+
+
+def test_mirror_needs_exact_x(ctx):
+    """With X truncated, T = S X is not symmetric: no mirror, and asking for it fails."""
+    pos, cell = synth.si_diamond_positions(2, np.random.default_rng(1))
+    s_exact = System(ctx, 4, "fp64", pos, cell, 6.6, 8.0, r_t=18.0)
+    assert s_exact.mirror
+    s_trunc = System(ctx, 4, "fp64", pos, cell, 6.6, 8.0, r_x=13.0)
+    assert not s_trunc.mirror
+    with pytest.raises(LnvError) as e:
+        s_trunc.set_mirror(True)
+    assert e.value.status == -5
+    s_trunc.set_mirror(False)
+
+
+def test_symmetric_product_needs_symmetric_pattern(ctx):
+    pos, cell = synth.si_diamond_positions(2, np.random.default_rng(0))
+    P = Pattern.build(ctx, pos, cell, 8.0)
+    rp, col = P.row_ptr.cpu().numpy(), P.col.cpu().numpy()
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    keep = col >= rows  # upper triangle only: not symmetric
+    nrp = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=len(rp) - 1))])
+    PU = Pattern.from_csr(ctx, nrp, col[keep])
+    with pytest.raises(LnvError) as e:
+        Plan(ctx, P, P, PU, sym_c=True)
+    assert e.value.status == -4
+
+
+def test_misaligned_value_arrays_are_refused(ctx):
+    """Value arrays off a 16-byte boundary are refused on the host (LNV_ERR_ARG)
+    before any kernel runs: the kernels move blocks in 16-byte pieces."""
+    pos, cell = synth.si_diamond_positions(2, np.random.default_rng(3))
+    P = Pattern.build(ctx, pos, cell, 6.6)
+    n = P.nnzb * 16
+    buf = torch.zeros(n + 4, dtype=torch.float32, device=ctx.device)
+    A = buf[1:1 + n].view(P.nnzb, 4, 4)
+    assert A.data_ptr() % 16 == 4
+    B = torch.zeros((P.nnzb, 4, 4), dtype=torch.float32, device=ctx.device)
+    with pytest.raises(LnvError) as e:
+        Plan(ctx, P, P, P).multiply(A, B)
+    assert e.value.status == -1
+    sysm = System(ctx, 4, "fp32", pos, cell, 6.6, 8.0)
+    L = torch.zeros((sysm.P_l.nnzb, 4, 4), dtype=torch.float32, device=ctx.device)
+    with pytest.raises(LnvError) as e:
+        sysm.energy_grad(A, B, L)
+    assert e.value.status == -1
+
+
 def test_plan_modes_follow_symbolic_counts(ctx):
     pos, cell = synth.si_diamond_positions(4, np.random.default_rng(0))
     P = {r: Pattern.build(ctx, pos, cell, r) for r in (6.6, 8.0, 14.6, 21.2)}
@@ -531,7 +620,7 @@ def test_minimisation_truncated_matches_oracle(ctx):
 # ------------------------------------------------------------------ truncated intermediates (next row)
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("r_x,r_t", [(4.5, 4.5), (5.0, 6.0), (6.0, 8.0), (None, None)])
+@pytest.mark.parametrize("r_x,r_t", [(4.5, 4.5), (5.0, 6.0), (6.0, 8.0), (None, 8.0), (None, None)])
 def test_truncated_system_matches_oracle(ctx, dtype, r_x, r_t):
     """512 atoms, R_SH = 3, R_L = 4.5: X, Y, Z kept within r_x and T, U within
     r_t, against the oracle's definition of the same truncation."""
