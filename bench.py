@@ -477,7 +477,7 @@ def run_batch64(args, ctx):
                    "cell_counts": counts, "mode": "one block-diagonal evaluation replayed as a CUDA graph",
                    "l2": "flushed between timed steps"},
         "gflops": round(flops * args.steps / t_graph / 1e9, 1),
-        "stage_kernels": {k: v[0] for k, v in tuned.items()},
+        "stage_kernels": {k: v[0] for k, v in tuned.items()}, "t_mirrored": sysb.mirror,
         "per_system_launches": {"value": round(n_atoms * args.steps / t_sep, 1), "unit": "atoms/s",
                                 "ms_per_step": round(t_sep * 1e3 / args.steps, 4)},
     }
@@ -550,7 +550,7 @@ def run_large(args, ctx, nsf, r_l, autograd):
                    "atoms": n_atoms, "nsf": nsf, "r_l": r_l,
                    "step": "autograd forward + recompute backward" if autograd else "energy + gradient"},
         "gflops": round(flops * args.steps / t / 1e9, 1),
-        "stage_kernels": {k: v[0] for k, v in tuned.items()},
+        "stage_kernels": {k: v[0] for k, v in tuned.items()}, "t_mirrored": sysm.mirror,
         "cpu_baseline": {"value": None, "kind": "oracle",
                          "reason": "not run: the FP64 oracle would hold every intermediate of 32768 atoms "
                                    "on the host (T alone is 86 M blocks) and take minutes (NSF=4) to tens "
@@ -593,7 +593,7 @@ def run_minimize(args, ctx, prec):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "atoms": n, "mu": mu, "timer": "host wall clock around the call "
                    "(the loop synchronises for its FP64 scalars every step)"},
-        "stage_kernels": {k: v[0] for k, v in tuned.items()},
+        "stage_kernels": {k: v[0] for k, v in tuned.items()}, "t_mirrored": sysm.mirror,
         "omega": {"start": float(hist[0, 0]), "end": float(hist[-1, 0])},
         "grad_rms": {"start": float(hist[0, 3]), "end": float(hist[-1, 3])},
     }
