@@ -155,14 +155,17 @@ lnv_status lnv_plan_product(lnv_ctx *ctx, const lnv_pattern *A, const lnv_patter
  * a hi/lo split of both operands, FP32 accumulation; FP32 values, NSF = 4;
  * other cases run kernel 3), 7 listed triples: per block of C the stored
  * (op(A)_ik, op(B)_kj) pairs, k ascending, listed once per plan (NSF = 4;
- * other NSF run kernel 0).
+ * other NSF run kernel 0), 8 kernel 5 with warp slices of half the width (8
+ * output columns per warp for two fused products, 16 for one): a warp lists
+ * only the k's its columns hit, and groups with few columns give more warps
+ * (other cases run kernel 3).
  * The default is 3 when at least half of the table's candidates hit, else 4,
  * when the tables fit a third of the free device memory. */
 lnv_status lnv_plan_info(const lnv_plan *plan, int64_t *triples, int *mode);
 /* Number of product kernels (0 .. LNV_NUM_KERNELS - 1). */
-#define LNV_NUM_KERNELS 8
-/* Select the kernel of a plan (0..7 as above); all give the same result up
- * to rounding order.  Kernels 3-5 build their tables on first selection
+#define LNV_NUM_KERNELS 9
+/* Select the kernel of a plan (0..8 as above); all give the same result up
+ * to rounding order.  Kernels 3-8 build their tables on first selection
  * (allocates, synchronises).  LNV_ERR_UNSUPPORTED if the kernel cannot run
  * this plan. */
 lnv_status lnv_plan_set_kernel(lnv_ctx *ctx, lnv_plan *plan, int kernel);

@@ -549,10 +549,12 @@ lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
         // triangle, then the mirror) and without (formed whole)
         for (int split = sg.pl->sym1; split >= 0 && st == LNV_OK; --split) {
             st = plan_set_split(ctx, sg.pl, split);
-            for (int k : {0, 2, 3, 4, 5, 6, 7}) {
+            for (int k : {0, 2, 3, 4, 5, 8, 6, 7}) {
                 if (st != LNV_OK) break;
                 // per-warp ring kernel: FP32 values, NSF = 4 (elsewhere kernel 5 is kernel 3)
                 if (k == 5 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
+                // its half-width form: the same cases
+                if (k == 8 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
                 // tensor-core kernel: FP32 values, NSF = 4 (3xTF32, FP32-level accuracy)
                 if (k == 6 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
                 // listed triples: NSF = 4 (elsewhere kernel 7 is kernel 0)

@@ -134,7 +134,8 @@ struct lnv_plan {
     // binary search per k, 2 pull with a merge-join walk (symmetric B pattern),
     // 3 row groups with a dense position table, 4 row groups with hit lists,
     // 5 row groups with per-warp lists, 6 row groups on tensor cores, 7
-    // listed triples per output block
+    // listed triples per output block, 8 kernel 5 with warp slices of half
+    // the width
     int mode;
     GroupPlan grp;
     TriplePlan tri;

@@ -271,7 +271,7 @@ lnv_status plan_pull_items(lnv_plan *pl)
 
 lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
 {
-    LNV_ARG(pl && kernel >= 0 && kernel < LNV_NUM_KERNELS, "kernel must be 0..7");
+    LNV_ARG(pl && kernel >= 0 && kernel < LNV_NUM_KERNELS, "kernel must be 0..8");
     if (kernel == 2) {
         if (!pl->B->symmetric) {
             set_error("the merge-join pull needs a symmetric B pattern");
@@ -312,7 +312,8 @@ void plan_trim(lnv_plan *plan)
 {
     if (plan->mode != 7) triple_plan_free(&plan->tri);
     GroupPlan &gp = plan->grp;
-    const bool dense = plan->mode == 3 || plan->mode == 5 || plan->mode == 6, sparse = plan->mode == 4;
+    const bool dense = plan->mode == 3 || plan->mode == 5 || plan->mode == 6 || plan->mode == 8,
+               sparse = plan->mode == 4;
     if (!dense && !sparse) {
         group_plan_free(&gp);
         return;

@@ -849,7 +849,9 @@ __device__ __forceinline__ void cp_async_wait()
 // Row-group product with independent warps (FP32, NSF = 4, G = 4 rows).
 //
 // A warp owns one slice of the group's output columns J: OPT sets of eight
-// consecutive columns (OPT = 2 for two fused products, 4 for one).  In a set,
+// consecutive columns (OPT = 2 for two fused products and 4 for one, or half
+// that: a warp then lists only the k's its narrower slice hits, and groups
+// with few columns give more warps).  In a set,
 // four lanes share a column j and lane r keeps column r of C_(m,j) for the G
 // rows m and NOUT products in registers.  Warps share nothing, so there is no
 // block-wide barrier: per chunk of KC k's of the group's K, the warp lists
@@ -866,11 +868,12 @@ __device__ __forceinline__ void cp_async_wait()
 // A is read the same way: rows of op(A), or of the stored block when
 // op(A) = A^T.  Sums run over k in ascending order (deterministic).  Outputs
 // (m, j) outside C's pattern are discarded at the store.
-template <int NOUT, int D, bool TA, bool TB>
+template <int NOUT, int OPT_, int D, bool TA, bool TB>
 struct GwShape {
-    static constexpr int G = 4, BS = 16, OPT = NOUT == 2 ? 2 : 4, COLS = 8 * OPT;
-    // k's per list chunk: eight two-warp CTAs fit an SM's 228 KB of shared memory
-    static constexpr int KC = NOUT == 2 ? 48 : 30;
+    static constexpr int G = 4, BS = 16, OPT = OPT_, COLS = 8 * OPT;
+    // k's per list chunk: one k per lane (the list is built in one pass of the
+    // warp), 30 where 32 would not let eight two-warp CTAs share an SM's 228 KB
+    static constexpr int KC = NOUT * OPT == 4 && NOUT == 1 ? 30 : 32;
     // list entry: k | set mask << 16 | row mask << 24, A's four block
     // positions, then op(B)_kj's block index per column (odd size: the
     // strided entry writes are free of bank conflicts)
@@ -887,7 +890,7 @@ __device__ __forceinline__ void cp_async16s(uint32_t dst, const void *src, int s
                  : "memory");
 }
 
-template <int NOUT, int D, int NW, bool TA, bool TB>
+template <int NOUT, int OPT_, int D, int NW, bool TA, bool TB>
 __global__ void __launch_bounds__(NW * 32, 16 / NW)
 k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
      const int64_t *__restrict__ j_off, const int32_t *__restrict__ j_list,
@@ -898,7 +901,7 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
      const float *__restrict__ b_val2, float *__restrict__ c_val1, float *__restrict__ c_val2,
      int64_t n_groups, const int32_t *__restrict__ jsplit, int part)
 {
-    using S = GwShape<NOUT, D, TA, TB>;
+    using S = GwShape<NOUT, OPT_, D, TA, TB>;
     constexpr int G = S::G, BS = S::BS, OPT = S::OPT, COLS = S::COLS, KC = S::KC, EW = S::EW;
     constexpr int STAGE = S::STAGE;
     static_assert((D & (D - 1)) == 0, "ring depth is a power of two");
@@ -1457,12 +1460,12 @@ lnv_status launch_grp(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const voi
     return LNV_OK;
 }
 
-template <int NOUT, bool TA, bool TB>
+template <int NOUT, int OPT, bool TA, bool TB>
 lnv_status launch_gw(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1, const void *B2,
                      void *C1, void *C2, int part)
 {
     constexpr int D = 4, NW = 2;
-    using S = GwShape<NOUT, D, TA, TB>;
+    using S = GwShape<NOUT, OPT, D, TA, TB>;
     const GroupPlan &gp = pl->grp;
     if (gp.n_groups == 0 || group_part_width(gp, part) == 0) return LNV_OK;
     if (!gp.bidx && gp.candidates > 0) {
@@ -1475,7 +1478,7 @@ lnv_status launch_gw(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void
     }
     const size_t smem = NW * S::warp_bytes;
     static_assert(8 * (NW * S::warp_bytes + 1024) <= 228 * 1024, "eight CTAs per SM");
-    auto kern = k_gw<NOUT, D, NW, TA, TB>;
+    auto kern = k_gw<NOUT, OPT, D, NW, TA, TB>;
     LNV_CUDA(ensure_smem((const void *)kern, smem));
     LNV_CUDA(prefer_smem((const void *)kern));
     kern<<<group_grid(gp.n_groups, group_part_width(gp, part), NW * S::COLS), NW * 32, smem, ctx->stream>>>(
@@ -1542,13 +1545,21 @@ lnv_status launch_group(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const v
         if (pl->mode == 6) return launch_gmma<NOUT, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
     }
     if constexpr (NSF == 4 && sizeof(T) == 4) {
-        if (pl->mode == 5) {
+        if (pl->mode == 5 || pl->mode == 8) {
+            // kernel 8: warp slices of half the width (8 columns for two
+            // products, 16 for one)
+            const bool half = pl->mode == 8;
             if (B2 && split && NOUT == 2) {
-                LNV_TRY((launch_gw<2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, 1)));
-                return launch_gw<1, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr, 2);
+                LNV_TRY(half ? (launch_gw<2, 1, TA, TB>(ctx, pl, A, B1, B2, C1, C2, 1))
+                             : (launch_gw<2, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, 1)));
+                return half ? launch_gw<1, 2, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr, 2)
+                            : launch_gw<1, 4, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr, 2);
             }
-            if (B2) return launch_gw<2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, part);
-            return launch_gw<1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, part);
+            if (B2)
+                return half ? launch_gw<2, 1, TA, TB>(ctx, pl, A, B1, B2, C1, C2, part)
+                            : launch_gw<2, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, part);
+            return half ? launch_gw<1, 2, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, part)
+                        : launch_gw<1, 4, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, part);
         }
     }
     if (pl->grp.G != 4) {

@@ -271,7 +271,8 @@ class Plan:
         _check(lib().lnv_plan_info(self.h, ctypes.byref(t), ctypes.byref(m)), "lnv_plan_info")
         self.triples, self.mode = t.value, self.KERNELS[m.value]
 
-    KERNELS = ("push", "pull", "pull-merge", "group", "group-sparse", "group-pipe", "group-mma", "triples")
+    KERNELS = ("push", "pull", "pull-merge", "group", "group-sparse", "group-pipe", "group-mma", "triples",
+               "group-pipe-half")
 
     def set_kernel(self, kernel):
         k = self.KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)

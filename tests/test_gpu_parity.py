@@ -109,7 +109,7 @@ PRODUCT_CASES = [
 
 
 @pytest.mark.parametrize("kernel", ["default", "push", "pull", "pull-merge", "group", "group-sparse",
-                                    "group-pipe", "group-mma", "triples"])
+                                    "group-pipe", "group-mma", "triples", "group-pipe-half"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("nsf", [1, 2, 4, 9])
 @pytest.mark.parametrize("case", PRODUCT_CASES)
@@ -134,7 +134,7 @@ def test_masked_product_matches_oracle(ctx, dtype, nsf, case, kernel):
 
 
 @pytest.mark.parametrize("kernel", ["default", "push", "pull", "pull-merge", "group", "group-sparse",
-                                    "group-pipe", "group-mma", "triples"])
+                                    "group-pipe", "group-mma", "triples", "group-pipe-half"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("nsf", [1, 4, 9])
 def test_symmetric_product_formed_on_one_triangle(ctx, dtype, nsf, kernel):
