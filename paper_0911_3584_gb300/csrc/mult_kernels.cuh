@@ -890,8 +890,17 @@ __device__ __forceinline__ void cp_async16s(uint32_t dst, const void *src, int s
                  : "memory");
 }
 
+// Resident CTAs per SM a k_gw shape is compiled for: 16 warps of up to 128
+// registers.  (24 warps of the half-width shapes, at 80 registers, ran 10-15%
+// slower: less room to keep loads in flight.)
+template <int NOUT, int OPT, int NW>
+constexpr int gw_min_blocks()
+{
+    return 16 / NW;
+}
+
 template <int NOUT, int OPT_, int D, int NW, bool TA, bool TB>
-__global__ void __launch_bounds__(NW * 32, 16 / NW)
+__global__ void __launch_bounds__(NW * 32, gw_min_blocks<NOUT, OPT_, NW>())
 k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
      const int64_t *__restrict__ j_off, const int32_t *__restrict__ j_list,
      const int32_t *__restrict__ cpos, const int64_t *__restrict__ bidx_off,
@@ -1464,6 +1473,7 @@ template <int NOUT, int OPT, bool TA, bool TB>
 lnv_status launch_gw(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1, const void *B2,
                      void *C1, void *C2, int part)
 {
+    // ring depth 4 (8 stages for the half-width shapes measured the same)
     constexpr int D = 4, NW = 2;
     using S = GwShape<NOUT, OPT, D, TA, TB>;
     const GroupPlan &gp = pl->grp;
@@ -1477,7 +1487,8 @@ lnv_status launch_gw(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void
         return LNV_ERR_UNSUPPORTED;
     }
     const size_t smem = NW * S::warp_bytes;
-    static_assert(8 * (NW * S::warp_bytes + 1024) <= 228 * 1024, "eight CTAs per SM");
+    constexpr int MINB = gw_min_blocks<NOUT, OPT, NW>();
+    static_assert(MINB * (NW * S::warp_bytes + 1024) <= 228 * 1024, "the CTAs of one SM fit its shared memory");
     auto kern = k_gw<NOUT, OPT, D, NW, TA, TB>;
     LNV_CUDA(ensure_smem((const void *)kern, smem));
     LNV_CUDA(prefer_smem((const void *)kern));
