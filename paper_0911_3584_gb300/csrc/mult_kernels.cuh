@@ -1561,10 +1561,12 @@ lnv_status launch_group(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const v
             // products, 16 for one)
             const bool half = pl->mode == 8;
             if (B2 && split && NOUT == 2) {
+                // the second product alone on the rest: half-width slices either
+                // way (they were the faster one-product form on every product
+                // measured)
                 LNV_TRY(half ? (launch_gw<2, 1, TA, TB>(ctx, pl, A, B1, B2, C1, C2, 1))
                              : (launch_gw<2, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, 1)));
-                return half ? launch_gw<1, 2, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr, 2)
-                            : launch_gw<1, 4, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr, 2);
+                return launch_gw<1, 2, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr, 2);
             }
             if (B2)
                 return half ? launch_gw<2, 1, TA, TB>(ctx, pl, A, B1, B2, C1, C2, part)
