@@ -912,6 +912,12 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
 {
     using S = GwShape<NOUT, OPT_, D, TA, TB>;
     constexpr int G = S::G, BS = S::BS, OPT = S::OPT, COLS = S::COLS, KC = S::KC, EW = S::EW;
+    // Row layout for the half-width shapes with op(B) = B: lane r keeps row r
+    // of C_mj (not column r), so it reads one row of each A block (one 16-byte
+    // read instead of four) and every B block whole (four 16-byte reads instead
+    // of four 4-byte ones).  It took XY from 1.17 to 1.11 ms; with op(B) = B^T,
+    // where the column layout reads B in one 16-byte read, it slowed Z and W.
+    constexpr bool ROWL = NOUT * OPT == 2 && !TB;
     constexpr int STAGE = S::STAGE;
     static_assert((D & (D - 1)) == 0, "ring depth is a power of two");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1062,6 +1068,54 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
             const int w0 = __shfl_sync(0xffffffffu, list[(size_t)q * EW], 0);
             const int om = (w0 >> 16) & 0xFF, mk = (w0 >> 24) & 0xF;
             const unsigned char *st = reinterpret_cast<const unsigned char *>(ring) + (q & (D - 1)) * STAGE * 4;
+            if constexpr (ROWL) {
+                // bq[o][n][z][y] = op(B)_kj[z][y]: the whole block, four 16-byte reads
+                float bq[OPT][NOUT][4][4];
+#pragma unroll
+                for (int o = 0; o < OPT; ++o) {
+                    if (!((om >> o) & 1)) continue;
+#pragma unroll
+                    for (int n = 0; n < NOUT; ++n) {
+                        const unsigned char *blk = st + ((o * NOUT + n) * 8 * BS + G * BS + jg * BS) * 4;
+#pragma unroll
+                        for (int rr = 0; rr < 4; ++rr) {
+                            const float4 v = *reinterpret_cast<const float4 *>(blk + ((rr + rot) & 3) * 16);
+                            const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                if (TB) bq[o][n][c][rr] = e[c];  // stored row rr = column rr of op(B)
+                                else bq[o][n][rr][c] = e[c];
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < G; ++m) {
+                    if (!((mk >> m) & 1)) continue;
+                    // a[z] = op(A)_mk[r][z]
+                    float a[4];
+                    if (TA) {
+#pragma unroll
+                        for (int z = 0; z < 4; ++z) a[z] = *reinterpret_cast<const float *>(st + (m * BS + z * 4 + r) * 4);
+                    } else {
+                        const float4 v = *reinterpret_cast<const float4 *>(st + (m * BS + r * 4) * 4);
+                        a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+                    }
+#pragma unroll
+                    for (int o = 0; o < OPT; ++o) {
+                        if (!((om >> o) & 1) || !((need >> (4 * o + m)) & 1)) continue;
+#pragma unroll
+                        for (int z = 0; z < 4; ++z)
+#pragma unroll
+                            for (int n = 0; n < NOUT; ++n)
+#pragma unroll
+                                for (int y = 0; y < 4; ++y)
+                                    acc[o][m][n][y] = fmaf(a[z], bq[o][n][z][y], acc[o][m][n][y]);
+                    }
+                }
+                __syncwarp();
+                continue;
+            }
             // bv[o][n][z] = op(B)[z][r]
             float bv[OPT][NOUT][4];
 #pragma unroll
@@ -1119,8 +1173,13 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
 #pragma unroll
             for (int n = 0; n < NOUT; ++n) {
                 float *dst = (n == 0 ? c_val1 : c_val2) + (int64_t)pos * BS;
+                if (ROWL) {
+                    *reinterpret_cast<float4 *>(dst + r * 4) =
+                        make_float4(acc[o][m][n][0], acc[o][m][n][1], acc[o][m][n][2], acc[o][m][n][3]);
+                } else {
 #pragma unroll
-                for (int x = 0; x < 4; ++x) dst[x * 4 + r] = acc[o][m][n][x];
+                    for (int x = 0; x < 4; ++x) dst[x * 4 + r] = acc[o][m][n][x];
+                }
             }
         }
     }
