@@ -455,6 +455,7 @@ def run_batch64(args, ctx):
     graph, out, G = sysb.capture(S, H, L)
     t_graph = _flush_timed(ctx, graph.replay, args.steps, args.warmup)
     flops = 2 * NSF ** 3 * sysb.triples(True)
+    mirrored = sysb.mirror
     del graph, sysb, S, H, L, out, G
     gc.collect()
     torch.cuda.empty_cache()
@@ -477,7 +478,7 @@ def run_batch64(args, ctx):
                    "cell_counts": counts, "mode": "one block-diagonal evaluation replayed as a CUDA graph",
                    "l2": "flushed between timed steps"},
         "gflops": round(flops * args.steps / t_graph / 1e9, 1),
-        "stage_kernels": {k: v[0] for k, v in tuned.items()}, "t_mirrored": sysb.mirror,
+        "stage_kernels": {k: v[0] for k, v in tuned.items()}, "t_mirrored": mirrored,
         "per_system_launches": {"value": round(n_atoms * args.steps / t_sep, 1), "unit": "atoms/s",
                                 "ms_per_step": round(t_sep * 1e3 / args.steps, 4)},
     }
