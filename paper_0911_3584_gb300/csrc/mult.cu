@@ -2,27 +2,26 @@
 //
 // The paper names sparse matrix multiplication as the main computational load
 // (Sec. 3) and K = 3LSL - 2LSLSL (Eq. 3) as the quantity built from it.  Each
-// product keeps only the blocks of C's range pattern.  Two kernels cover the
-// products of the LNV evaluation, chosen per plan from symbolic counts:
+// product keeps only the blocks of C's range pattern.  This file holds the
+// symbolic pass, the plans and the dispatch; the kernels are in
+// mult_kernels.cuh:
 //
-//  push  one CTA per output row i.  The row (in column chunks) is accumulated
-//        in shared memory: for each k of A's row i (serially), the threads
-//        spread over the blocks (k, j) of B's row k that fall in the chunk's
-//        column range, find j's slot by binary search in the staged column
-//        list and add A_ik B_kj.  Within one k every j is distinct, so no two
-//        threads touch one slot; a barrier separates successive k.  Sums are
-//        formed in k order (deterministic).  Best when B's rows fit C's row:
-//        X = LS, Y = LH, T = SX, U = SY (full-range products).
+//  0  push: one CTA per (output row, column chunk), the chunk accumulated in
+//     shared memory; warps own column slices, so no two lanes touch one slot
+//     within a k.  Best for full-range products (X = LS, T = SX) in FP64.
+//  1  pull with a binary search per k; 2 pull with a merge-join walk of B's
+//     row j (symmetric B): output owners, for narrow C rows.
+//  3, 4  row groups of 4 rows (position table or hit lists): one fetch of
+//     op(B)_kj serves every row of the group holding A_ik.
+//  5, 8  row groups with independent warps, per-warp k lists and a cp.async
+//     ring (FP32, NSF = 4); kernel 8 with warp slices of half the width.
+//  6  row groups on TF32 tensor cores (mma.sync, hi/lo split).
+//  7  listed triples: per output block its (A, B) pairs, listed once per plan.
 //
-//  pull  one CTA per output row i, each thread owns OPT consecutive output
-//        blocks (i, j) and accumulates them in registers over k of A's row i
-//        (staged in shared memory in chunks).  For each k the thread finds
-//        its j's in B's sorted row k (binary search, then galloping), so the
-//        candidates tested are |A row| x |C row|.  Best when C's row is
-//        narrow: Z = L T masked to R_X, W = X^T U^T and Q = H Z masked to R_L.
-//
-// Operand transposes (op = ^T) read block (k, i) through the pattern's
-// transpose map and transpose it in registers.
+// A product declared symmetric (LNV_SYM_C, T = SLS) may be formed on its
+// upper triangle and mirrored (mirror_lower).  Sums are formed in k order in
+// every kernel (deterministic).  Operand transposes (op = ^T) read block
+// (k, i) through the pattern's transpose map.
 #include <algorithm>
 #include <type_traits>
 #include <cstring>

@@ -51,79 +51,6 @@ __device__ __forceinline__ void load_row(const T *__restrict__ blk, int z, T (&r
     for (int y = 0; y < NSF; ++y) r[y] = TR ? __ldg(blk + y * NSF + z) : __ldg(blk + z * NSF + y);
 }
 
-// ------------------------------------------------------------------ push
-
-template <typename T, int NSF, int NOUT, bool TA, bool TB>
-__global__ void __launch_bounds__(128)
-k_push(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
-       const int64_t *__restrict__ a_tr, const T *__restrict__ a_val,
-       const int64_t *__restrict__ b_rp, const int32_t *__restrict__ b_col,
-       const int64_t *__restrict__ b_tr, const T *__restrict__ b_val1,
-       const T *__restrict__ b_val2, const int64_t *__restrict__ c_rp,
-       const int32_t *__restrict__ c_col, T *__restrict__ c_val1, T *__restrict__ c_val2,
-       int chunk)
-{
-    constexpr int BS = NSF * NSF;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *acc = reinterpret_cast<T *>(smem_raw);                  // [NOUT][chunk][BS]
-    T *a_s = acc + (size_t)NOUT * chunk * BS;                  // [BS]
-    int32_t *ccol = reinterpret_cast<int32_t *>(a_s + BS);     // [chunk]
-
-    const int64_t i = blockIdx.x;
-    const int64_t cb = c_rp[i], ce = c_rp[i + 1];
-    const int64_t ab = a_rp[i], ae = a_rp[i + 1];
-    for (int64_t c0 = cb; c0 < ce; c0 += chunk) {
-        const int cn = (int)min((int64_t)chunk, ce - c0);
-        for (int t = threadIdx.x; t < cn; t += blockDim.x) ccol[t] = c_col[c0 + t];
-        for (int t = threadIdx.x; t < NOUT * cn * BS; t += blockDim.x) {
-            int o = t / (cn * BS), r = t - o * cn * BS;
-            acc[(size_t)o * chunk * BS + r] = T(0);
-        }
-        __syncthreads();
-        const int32_t jlo = ccol[0], jhi = ccol[cn - 1];
-        for (int64_t q = ab; q < ae; ++q) {
-            const int32_t k = a_col[q];
-            if (threadIdx.x < BS) {
-                int x = threadIdx.x / NSF, z = threadIdx.x % NSF;
-                a_s[threadIdx.x] = TA ? a_val[a_tr[q] * BS + z * NSF + x] : a_val[q * BS + threadIdx.x];
-            }
-            const int64_t bb = b_rp[k], be = b_rp[k + 1];
-            const int64_t lo = lower_bound_g(b_col, bb, be, jlo);
-            const int64_t hi = lower_bound_g(b_col, lo, be, jhi + 1);
-            __syncthreads();
-            for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-                const int32_t j = b_col[p];
-                const int s = lower_bound_s(ccol, cn, j);
-                if (s >= cn || ccol[s] != j) continue;
-                const int64_t pb = TB ? b_tr[p] : p;
-#pragma unroll
-                for (int o = 0; o < NOUT; ++o) {
-                    const T *bblk = (o == 0 ? b_val1 : b_val2) + pb * BS;
-                    T *ac = acc + ((size_t)o * chunk + s) * BS;
-#pragma unroll
-                    for (int z = 0; z < NSF; ++z) {
-                        T br[NSF];
-                        load_row<T, NSF, TB>(bblk, z, br);
-#pragma unroll
-                        for (int x = 0; x < NSF; ++x) {
-                            const T ax = a_s[x * NSF + z];
-#pragma unroll
-                            for (int y = 0; y < NSF; ++y) ac[x * NSF + y] = fma(ax, br[y], ac[x * NSF + y]);
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-        }
-        for (int t = threadIdx.x; t < NOUT * cn * BS; t += blockDim.x) {
-            int o = t / (cn * BS), r = t - o * cn * BS;
-            T *dst = o == 0 ? c_val1 : c_val2;
-            dst[c0 * BS + r] = acc[(size_t)o * chunk * BS + r];
-        }
-        __syncthreads();
-    }
-}
-
 // ------------------------------------------------------------------ pull
 
 template <typename T, int NSF, int OPT, bool TA, bool TB>
@@ -222,7 +149,10 @@ k_pull(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
 // (block, output row x, product) tasks of the sub-range: within one k every
 // column j is distinct, so no two lanes touch one accumulator row, and a
 // __syncwarp separates successive k.  Each slot therefore sums its k's in order
-// (deterministic) and no CTA-wide barrier is needed inside the k loop.
+// (deterministic) and no CTA-wide barrier is needed inside the k loop.  SYM:
+// the first output is symmetric and only its blocks with j >= i are formed
+// (a further bound per k marks the diagonal in B's row); the lower triangle
+// is mirrored afterwards.
 template <typename T, int NSF, int NOUT, bool TA, bool TB, int NW, bool SYM>
 __global__ void __launch_bounds__(NW * 32)
 k_push2(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
@@ -1425,31 +1355,6 @@ template <typename T, int NSF>
 constexpr int pull_opt()
 {
     return NSF >= 9 ? 1 : (sizeof(T) == 8 ? 2 : (NSF <= 2 ? 4 : 4));
-}
-
-template <typename T, int NSF, int NOUT, bool TA, bool TB>
-lnv_status launch_push(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
-                       const void *B2, void *C1, void *C2)
-{
-    constexpr int BS = NSF * NSF;
-    const lnv_pattern *PA = pl->A, *PB = pl->B, *PC = pl->C;
-    if (PC->n == 0) return LNV_OK;
-    size_t budget = std::min<size_t>(ctx->smem_optin, 96 * 1024);
-    size_t per_slot = (size_t)NOUT * BS * sizeof(T) + sizeof(int32_t);
-    size_t fixed = BS * sizeof(T) + 64;
-    int chunk = (int)std::min<size_t>((budget - fixed) / per_slot, (size_t)std::max(pl->max_c_row, 1));
-    if (chunk < 1) {
-        set_error("push product: shared memory too small for one block");
-        return LNV_ERR_UNSUPPORTED;
-    }
-    size_t smem = (size_t)NOUT * chunk * BS * sizeof(T) + BS * sizeof(T) + sizeof(int32_t) * chunk + 16;
-    auto kern = k_push<T, NSF, NOUT, TA, TB>;
-    LNV_CUDA(ensure_smem((const void *)kern, smem));
-    kern<<<(unsigned)PC->n, kThreads, smem, ctx->stream>>>(
-        PA->row_ptr, PA->col, PA->tr, (const T *)A, PB->row_ptr, PB->col, PB->tr, (const T *)B1,
-        (const T *)B2, PC->row_ptr, PC->col, (T *)C1, (T *)C2, chunk);
-    LNV_LAUNCHED();
-    return LNV_OK;
 }
 
 template <typename T, int NSF, bool TA, bool TB>
