@@ -282,8 +282,9 @@ lnv_status lnv_system_stage_ms(lnv_system *sys, double *ms7);
 
 /* One evaluation (Sec. 2, Eq. 3).  S_dev, H_dev (on the r_sh pattern) and
  * L_dev (on the r_l pattern) are value arrays in the system's precision.
- * All three are symmetric, as the overlap, the Hamiltonian and the auxiliary
- * density matrix are: block (j, i) is the transpose of block (i, j).  The
+ * All three must be symmetric (block (j, i) the transpose of block (i, j)),
+ * as the overlap and Hamiltonian of real basis functions are and as L is
+ * taken, so that K is a symmetric density matrix.  The
  * evaluation relies on it (T = SLS is formed on one triangle and mirrored, and
  * Z = L T is read as L T^T); the results for a non-symmetric L are
  * undefined.
