@@ -257,7 +257,9 @@ def roofline(res):
     tr = ncu_traffic(stage, prec)
     return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 3), "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4), "traffic": tr,
-            "kernel": f"{KERNEL_NAME[res['kernels'][stage]]} ({STAGE_KERNEL[stage]})",
+            "kernel": f"{KERNEL_NAME[res['kernels'][stage]]} ({STAGE_KERNEL[stage]})"
+                      + (" on T's upper triangle, then k_mirror_lower" if stage == "TU" and res["t_mirrored"]
+                         else ""),
             "stage": stage, "kernel_ms": round(ms, 4),
             "algorithmic_flops_per_launch": res["flops_stage"][stage],
             "peak_source": ("derived: 152 SMs x 2.07 GHz x 256 flop/clk/SM (FP32 FMA)" if prec == "fp32"
