@@ -187,6 +187,23 @@ def test_overlap_is_positive_definite():
     assert np.allclose(Sd, Sd.T)
 
 
+@pytest.mark.parametrize("ncell,nsf", [(8, 4), (4, 9)])
+def test_overlap_is_positive_definite_at_benchmark_sizes(ncell, nsf):
+    """S of the 4096-atom benchmark workload (and of an NSF = 9 system) is
+    symmetric and positive definite: its smallest eigenvalue, from Lanczos on
+    the sparse matrix, is bounded away from zero.  Diagonal dominance alone
+    does not guarantee it for every row."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+
+    w, S, H, L = _si(ncell, nsf, 6.6, 8.0, seed=0)
+    n = (len(S["rp"]) - 1) * nsf
+    M = sp.bsr_matrix((S["val"], S["col"], S["rp"]), shape=(n, n)).tocsr()
+    assert abs(M - M.T).max() == 0.0
+    lam = sla.eigsh(M, k=1, which="SA", return_eigenvectors=False, tol=1e-8)[0]
+    assert lam > 0.5, lam
+
+
 def _dense_system(nsf=4, seed=11):
     """One 8-atom cell with every range past the box: all matrices dense."""
     w, S, H, L = _si(1, nsf, 5.0, 5.0, seed=seed)
