@@ -138,9 +138,8 @@ lnv_status lnv_pattern_remap(lnv_ctx *ctx, const lnv_pattern *from, const lnv_pa
  * the diagonal of the full matrix is then set to its mirror element (blocks
  * (i, j), j < i, to the transpose of block (j, i)), so the result is exactly
  * symmetric.  The caller vouches for the symmetry: the lower triangle is not
- * computed.  The plan
- * chooses a row-gather ("push") or output-owner ("pull") kernel from the
- * patterns' symbolic work counts.  The patterns must outlive the plan.
+ * computed.  The plan chooses its kernel from the patterns' symbolic work
+ * counts (see lnv_plan_info).  The patterns must outlive the plan.
  * Synchronises. */
 lnv_status lnv_plan_product(lnv_ctx *ctx, const lnv_pattern *A, const lnv_pattern *B,
                             const lnv_pattern *C, int flags, lnv_plan **out);
