@@ -336,10 +336,23 @@ def si4096():
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_lnv_4096_atoms_full(ctx, si4096, dtype):
-    """The benchmark workload (8x8x8 cells, 4096 atoms, NSF=4, R_L = 8 A) in the
-    launch configuration the benchmark times, every output against the oracle."""
+    """The benchmark workload (8x8x8 cells, 4096 atoms, NSF=4, R_L = 8 A) with
+    the plans' default kernels, every output against the oracle."""
     w, ref = si4096
     _, out, G = _gpu_lnv(ctx, w, dtype)
+    _check_lnv(out, G, ref, dtype)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_lnv_4096_atoms_bench_configuration(ctx, si4096, dtype):
+    """The benchmark workload in the launch configuration bench.py times: the
+    system autotuned the same way (kernel per product, T mirrored or whole),
+    then every output against the oracle."""
+    w, ref = si4096
+    sysm = System(ctx, w["nsf"], PREC[dtype], w["pos"], w["cell"], w["r_sh"], w["r_l"])
+    S, H, L = (to_dev(w[k], dtype, ctx.device) for k in ("S", "H", "L"))
+    sysm.autotune(S, H, L, reps=2)
+    _, out, G = _gpu_lnv(ctx, w, dtype, sysm=sysm)
     _check_lnv(out, G, ref, dtype)
 
 
