@@ -5,6 +5,8 @@ relative error <= 1e-10 for E and N_e; FP32 path (FP32 products, FP64 traces
 and gradient combination), <= 2e-5 for both, measured against the oracle run
 on the FP64 inputs.  Integer work (patterns, transpose maps) is bit-exact.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -354,6 +356,32 @@ def test_lnv_4096_atoms_bench_configuration(ctx, si4096, dtype):
     sysm.autotune(S, H, L, reps=2)
     _, out, G = _gpu_lnv(ctx, w, dtype, sysm=sysm)
     _check_lnv(out, G, ref, dtype)
+
+
+@pytest.mark.skipif(os.environ.get("LNV_FULL_SIZE_TESTS") != "1",
+                    reason="32768-atom sampled parity: set LNV_FULL_SIZE_TESTS=1 (minutes, 16 GB of host memory)")
+@pytest.mark.parametrize("nsf", [4, 9])
+def test_32768_atoms_sampled_rows_bench_configuration(ctx, nsf):
+    """The 16x16x16-cell workloads (32768 atoms, R_SH = 6.6 A, R_L = 10 A,
+    NSF = 4 and 9) in the configuration bench.py times them (FP32, autotuned):
+    dE/dL and dN_e/dL on the rows of three atoms against the row-chain oracle
+    (oracle/sampled.py), which forms those rows from the definition."""
+    from oracle.sampled import lnv_grad_rows
+
+    w = synth.si_workload(16, nsf, 6.6, 10.0, 0, oracle.pattern)
+    sysm = System(ctx, nsf, "fp32", w["pos"], w["cell"], 6.6, 10.0)
+    assert np.array_equal(sysm.P_l.col.cpu().numpy(), w["l_col"])
+    Sd, Hd, Ld = (to_dev(w[k], torch.float32, ctx.device) for k in ("S", "H", "L"))
+    sysm.autotune(Sd, Hd, Ld, reps=1)
+    out, G, GN = sysm.energy_grad(Sd, Hd, Ld, grad=True, grad_ne=True)
+    S, H, L = (oracle.csr(w[rp], w[c], w[k].astype(np.float32).astype(np.float64))
+               for rp, c, k in (("sh_row_ptr", "sh_col", "S"), ("sh_row_ptr", "sh_col", "H"),
+                                ("l_row_ptr", "l_col", "L")))
+    ref = lnv_grad_rows(S, H, L, [7, 16411, 32767])
+    g = G.double().cpu().numpy()[ref["pos"]]
+    gn = GN.double().cpu().numpy()[ref["pos"]]
+    assert rel_fro(g, ref["G"]) <= TOL[torch.float32][0]
+    assert rel_fro(gn, ref["GN"]) <= TOL[torch.float32][0]
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])

@@ -204,6 +204,39 @@ def test_overlap_is_positive_definite_at_benchmark_sizes(ncell, nsf):
     assert lam > 0.5, lam
 
 
+# ---------------------------------------------------------------- sampled gradient rows
+
+@pytest.mark.parametrize("ncell,nsf,r_sh,r_l", [(2, 4, 6.6, 8.0), (2, 9, 4.0, 5.0), (1, 4, 5.0, 5.0)])
+def test_sampled_gradient_rows_match_dense_definition(ncell, nsf, r_sh, r_l):
+    """The row-chain gradient (oracle/sampled.py) equals the dense definition
+    of G and dN_e/dL, read on L's pattern, for chosen atoms."""
+    from oracle.sampled import lnv_grad_rows
+
+    w, S, H, L = _si(ncell, nsf, r_sh, r_l, seed=4)
+    Sd, Hd, Ld = (to_dense(M["rp"], M["col"], M["val"]) for M in (S, H, L))
+    _, _, Gd, _ = lnv_dense(Sd, Hd, Ld)
+    G = from_dense(Gd, L["rp"], L["col"], nsf)
+    GN = from_dense(ne_grad_dense(Sd, Ld), L["rp"], L["col"], nsf)
+    n = L["rp"].size - 1
+    r = lnv_grad_rows(S, H, L, [0, n // 2, n - 1])
+    assert np.array_equal(r["pos"], np.concatenate([np.arange(L["rp"][a], L["rp"][a + 1]) for a in (0, n // 2, n - 1)]))
+    assert np.linalg.norm(r["G"] - G[r["pos"]]) <= 1e-12 * np.linalg.norm(G[r["pos"]])
+    assert np.linalg.norm(r["GN"] - GN[r["pos"]]) <= 1e-12 * np.linalg.norm(GN[r["pos"]])
+
+
+def test_sampled_gradient_rows_match_full_oracle_512_atoms():
+    """On the 512-atom workload (too large to form densely here), the row
+    chain and the masked-product plan agree on sampled rows."""
+    from oracle.sampled import lnv_grad_rows
+
+    w, S, H, L = _si(4, 4, 6.6, 8.0, seed=0)
+    ref = oracle.lnv_energy_grad(w["pos"], w["cell"], 6.6, 8.0, S, H, L, grad=True, grad_ne=True)
+    r = lnv_grad_rows(S, H, L, [3, 200, 511])
+    g, gn = ref["G"][r["pos"]], ref["GN"][r["pos"]]
+    assert np.linalg.norm(r["G"] - g) <= 1e-12 * np.linalg.norm(g)
+    assert np.linalg.norm(r["GN"] - gn) <= 1e-12 * np.linalg.norm(gn)
+
+
 def _dense_system(nsf=4, seed=11):
     """One 8-atom cell with every range past the box: all matrices dense."""
     w, S, H, L = _si(1, nsf, 5.0, 5.0, seed=seed)
