@@ -35,7 +35,8 @@ STAGE_KERNEL = {"XY": "X=LS, Y=LH", "TU": "T=SX, U=SY", "Z": "Z=L T^T", "Q": "Q=
                 "W": "W=X^T U^T"}
 KERNEL_NAME = {"push": "k_push2", "pull": "k_pull", "pull-merge": "k_pull2", "group": "k_grp",
                "group-sparse": "k_grp (hit lists)", "group-pipe": "k_gw", "group-mma": "k_gmma",
-               "triples": "k_tri", "group-pipe-half": "k_gw (half-width slices)"}
+               "triples": "k_tri", "group-pipe-half": "k_gw (half-width slices)",
+               "tensor": "k_umma (tcgen05, 3xTF32)"}
 
 
 def parse():

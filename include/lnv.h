@@ -52,6 +52,8 @@ typedef int lnv_status;
 #define LNV_ERR_PATTERN (-4)     /* patterns of different sizes, unsorted or
                                     non-symmetric where symmetry is needed  */
 #define LNV_ERR_UNSUPPORTED (-5) /* NSF or precision not built, row too long */
+#define LNV_ERR_TIMEOUT (-6)     /* a bounded device-side wait ran out (see
+                                    lnv_ctx_device_status)                  */
 
 /* Arithmetic of a call.  LNV_FP64: values, products and sums in FP64.
  * LNV_FP32: values stored and multiplied in FP32 with FP32 accumulation of
@@ -85,6 +87,23 @@ const char *lnv_last_error(void);
 const char *lnv_version(void);
 /* Kernels this library has launched in this process so far (all threads). */
 int64_t lnv_launch_count(void);
+
+/* Device-side status of the context.  The tensor-core product kernel (kernel
+ * 9 below) synchronises its warps with barriers whose waits are bounded in
+ * time: a wait that runs out (which only a fault elsewhere, e.g. a kernel
+ * killed mid-way, can cause) makes the kernel drain its in-flight work, free
+ * its tensor memory and exit, with its outputs undefined, and raises the
+ * context's status word.  lnv_ctx_device_status synchronises the context
+ * stream, returns LNV_ERR_TIMEOUT if the word was raised since the last call
+ * (and clears it), else LNV_OK.  lnv_ctx_set_wait_limit sets the limit of one
+ * wait in nanoseconds (default 1 s; > 0). */
+lnv_status lnv_ctx_device_status(lnv_ctx *ctx);
+lnv_status lnv_ctx_set_wait_limit(lnv_ctx *ctx, uint64_t ns);
+/* Exercise the bounded-wait path: one CTA waits on a barrier that nothing
+ * completes, gives up after the context's wait limit and raises the status
+ * word (no fault, no trap).  Asynchronous; read the result with
+ * lnv_ctx_device_status. */
+lnv_status lnv_debug_expire_wait(lnv_ctx *ctx);
 
 /* ---- a0: range patterns (Sec. 2, locality of L and of the products) ---- */
 
@@ -157,14 +176,20 @@ lnv_status lnv_plan_product(lnv_ctx *ctx, const lnv_pattern *A, const lnv_patter
  * other NSF run kernel 0), 8 kernel 5 with warp slices of half the width (8
  * output columns per warp for two fused products, 16 for one): a warp lists
  * only the k's its columns hit, and groups with few columns give more warps
- * (other cases run kernel 3).
+ * (other cases run kernel 3), 9 row groups of 8 atoms as dense tiles on the
+ * tcgen05 tensor cores: C_g^T = op(B)^T op(A)_g^T with 128-row tiles of 32
+ * output columns j, op(B) rows gathered into tensor memory, op(A) in shared
+ * memory, every operand split into TF32 high and low parts (hi*hi + hi*lo +
+ * lo*hi, FP32 accumulation: FP32-level accuracy); needs op(B) = B^T (plans
+ * without LNV_TRANS_B fail with LNV_ERR_UNSUPPORTED); FP32 values with NSF =
+ * 4 (other cases run kernel 0).
  * The default is 3 when at least half of the table's candidates hit, else 4,
  * when the tables fit a third of the free device memory. */
 lnv_status lnv_plan_info(const lnv_plan *plan, int64_t *triples, int *mode);
 /* Number of product kernels (0 .. LNV_NUM_KERNELS - 1). */
-#define LNV_NUM_KERNELS 9
-/* Select the kernel of a plan (0..8 as above); all give the same result up
- * to rounding order.  Kernels 3-8 build their tables on first selection
+#define LNV_NUM_KERNELS 10
+/* Select the kernel of a plan (0..9 as above); all give the same result up
+ * to rounding order.  Kernels 3-9 build their tables on first selection
  * (allocates, synchronises).  LNV_ERR_UNSUPPORTED if the kernel cannot run
  * this plan. */
 lnv_status lnv_plan_set_kernel(lnv_ctx *ctx, lnv_plan *plan, int kernel);

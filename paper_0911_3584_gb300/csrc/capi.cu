@@ -182,7 +182,35 @@ lnv_status lnv_ctx_create(int device, void *cuda_stream, lnv_ctx **out)
     c->sm_count = v;
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     c->smem_optin = (size_t)v;
+    cudaError_t e = cudaMalloc(&c->dev_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->dev_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(c->dev_status);
+        delete c;
+        set_error("context status word: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? LNV_ERR_OOM : LNV_ERR_CUDA;
+    }
     *out = c;
+    return LNV_OK;
+}
+
+lnv_status lnv_ctx_device_status(lnv_ctx *ctx)
+{
+    LNV_TRY(set_dev(ctx));
+    int h = 0;
+    LNV_CUDA(cudaMemcpyAsync(&h, ctx->dev_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    LNV_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (h == 0) return LNV_OK;
+    LNV_CUDA(cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), ctx->stream));
+    LNV_CUDA(cudaStreamSynchronize(ctx->stream));
+    set_error("a device-side wait ran out; the outputs of the kernels since the last check are undefined");
+    return LNV_ERR_TIMEOUT;
+}
+
+lnv_status lnv_ctx_set_wait_limit(lnv_ctx *ctx, uint64_t ns)
+{
+    LNV_ARG(ctx && ns > 0, "wait limit must be positive");
+    ctx->wait_ns = (unsigned long long)ns;
     return LNV_OK;
 }
 
@@ -195,7 +223,10 @@ lnv_status lnv_ctx_set_stream(lnv_ctx *ctx, void *cuda_stream)
 
 lnv_status lnv_ctx_destroy(lnv_ctx *ctx)
 {
-    if (ctx) cudaFree(ctx->scratch);
+    if (ctx) {
+        cudaFree(ctx->scratch);
+        cudaFree(ctx->dev_status);
+    }
     delete ctx;
     return LNV_OK;
 }
@@ -549,8 +580,10 @@ lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
         // triangle, then the mirror) and without (formed whole)
         for (int split = sg.pl->sym1; split >= 0 && st == LNV_OK; --split) {
             st = plan_set_split(ctx, sg.pl, split);
-            for (int k : {0, 2, 3, 4, 5, 8, 6, 7}) {
+            for (int k : {0, 2, 3, 4, 5, 8, 6, 7, 9}) {
                 if (st != LNV_OK) break;
+                // tcgen05 kernel: one FP32 product with NSF = 4 and op(B) = B^T
+                if (k == 9 && (sys->nsf != 4 || sys->prec != LNV_FP32 || !sg.pl->trans_b || sg.B2)) continue;
                 // per-warp ring kernel: FP32 values, NSF = 4 (elsewhere kernel 5 is kernel 3)
                 if (k == 5 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
                 // its half-width form: the same cases

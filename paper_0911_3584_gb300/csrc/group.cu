@@ -116,8 +116,9 @@ void group_plan_free(GroupPlan *gp)
     *gp = GroupPlan();
 }
 
-// Lists (K, J, apos, cpos) and hit counts of the row groups: built once per plan.
-static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes)
+// Lists (K, J, apos, cpos) and hit counts of the row groups: built once per plan
+// into gp (the plan's 4-row tables, or the 8-row tables of kernel 9).
+static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes, GroupPlan &gp)
 {
     const lnv_pattern *A = pl->A, *B = pl->B, *C = pl->C;
     if (B->max_row >= 0xFFFF) {
@@ -168,7 +169,7 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
     }
     // symmetric first output: the upper part of J (j >= the group's first row)
     // comes first, and jsplit[g] (a multiple of 8) is where the rest starts
-    const bool split = pl->sym1 && pl->split;
+    const bool split = pl->sym1 && pl->split && &gp == &pl->grp;
     std::vector<int32_t> jsplit(split ? ng : 0);
     std::vector<int32_t> k_list(k_off[ng]), j_list(j_off[ng]);
     std::vector<int32_t> apos((size_t)k_off[ng] * G, -1), cpos((size_t)j_off[ng] * G, -1);
@@ -226,7 +227,6 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
             });
         for (auto &x : th) x.join();
     }
-    GroupPlan &gp = pl->grp;
     gp.G = G;
     gp.n_groups = ng;
     gp.max_k = max_k;
@@ -280,11 +280,11 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
 
 // Build the lists (once) and the requested forms: the dense 16-bit position
 // table and / or the hit lists.  Each form is checked against the budget.
-lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes, bool dense,
-                            bool sparse)
+lnv_status group_plan_build_into(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes, bool dense, bool sparse,
+                                 GroupPlan &gp)
 {
-    GroupPlan &gp = pl->grp;
-    if (gp.G == 0) LNV_TRY(group_plan_lists(ctx, pl, G, budget_bytes));
+    if (gp.G != 0 && gp.G != G) group_plan_free(&gp);
+    if (gp.G == 0) LNV_TRY(group_plan_lists(ctx, pl, G, budget_bytes, gp));
     const lnv_pattern *B = pl->B;
     const int64_t ng = gp.n_groups;
     if (dense && !gp.bidx && gp.candidates > 0) {
@@ -316,6 +316,11 @@ lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_byt
         gp.bytes += need;
     }
     return LNV_OK;
+}
+
+lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes, bool dense, bool sparse)
+{
+    return group_plan_build_into(ctx, pl, G, budget_bytes, dense, sparse, pl->grp);
 }
 
 }  // namespace lnv

@@ -63,6 +63,10 @@ struct lnv_ctx {
     cudaStream_t stream;
     int sm_count;
     size_t smem_optin;
+    // device status word: set to 1 by a kernel whose bounded device-side wait
+    // ran out (read and cleared by lnv_ctx_device_status)
+    int *dev_status = nullptr;
+    unsigned long long wait_ns = 1000000000ull;  // limit of one device-side wait
     double *scratch = nullptr;  // reduction partials of lnv_vec_dot (grown on demand)
     size_t scratch_n = 0;
 };
@@ -135,9 +139,10 @@ struct lnv_plan {
     // 3 row groups with a dense position table, 4 row groups with hit lists,
     // 5 row groups with per-warp lists, 6 row groups on tensor cores, 7
     // listed triples per output block, 8 kernel 5 with warp slices of half
-    // the width
+    // the width, 9 8-row groups on the tcgen05 tensor cores (tables in tc)
     int mode;
     GroupPlan grp;
+    GroupPlan tc;  // 8-row groups of the tensor-core kernel (9)
     TriplePlan tri;
     // work items (row, first output slot) of the merge-join pull, for 64 and
     // 128 outputs per CTA (device arrays)
@@ -190,6 +195,11 @@ lnv_status plan_set_split(lnv_ctx *ctx, lnv_plan *pl, int on);
 // not fit the budget or a B row is too long for 16-bit offsets.
 lnv_status group_plan_build(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes, bool dense,
                             bool sparse);
+lnv_status group_plan_build_into(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budget_bytes, bool dense, bool sparse,
+                                 GroupPlan &gp);
+// Kernel 9 (umma.cu): C = mask(op(A) B^T) on 8-row groups, tcgen05 tensor
+// cores, FP32 values, NSF = 4.
+lnv_status launch_umma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B, void *C);
 lnv_status scan_exclusive(cudaStream_t st, const int64_t *in, int64_t n, int64_t *out);
 void group_plan_free(GroupPlan *gp);
 // Triple-list plan (triples.cu); LNV_ERR_UNSUPPORTED when it would not fit the budget.

@@ -17,6 +17,8 @@
 //     ring (FP32, NSF = 4); kernel 8 with warp slices of half the width.
 //  6  row groups on TF32 tensor cores (mma.sync, hi/lo split).
 //  7  listed triples: per output block its (A, B) pairs, listed once per plan.
+//  9  row groups of 8 rows as dense tiles on the tcgen05 tensor cores (umma.cu):
+//     FP32 values, NSF = 4, op(B) = B^T, split-TF32 operands.
 //
 // A product declared symmetric (LNV_SYM_C, T = SLS) may be formed on its
 // upper triangle and mirrored (mirror_lower).  Sums are formed in k order in
@@ -270,7 +272,7 @@ lnv_status plan_pull_items(lnv_plan *pl)
 
 lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
 {
-    LNV_ARG(pl && kernel >= 0 && kernel < LNV_NUM_KERNELS, "kernel must be 0..8");
+    LNV_ARG(pl && kernel >= 0 && kernel < LNV_NUM_KERNELS, "kernel must be 0..9");
     if (kernel == 2) {
         if (!pl->B->symmetric) {
             set_error("the merge-join pull needs a symmetric B pattern");
@@ -278,7 +280,17 @@ lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
         }
         LNV_TRY(plan_pull_items(pl));
     }
-    if (kernel == 7) {
+    if (kernel == 9) {
+        // 8-row group tables with the dense position table; the kernel reads
+        // op(B) = B^T only (rows of the stored B_jk)
+        if (!pl->trans_b) {
+            set_error("kernel 9 needs a product with op(B) = B^T");
+            return LNV_ERR_UNSUPPORTED;
+        }
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        LNV_TRY(group_plan_build_into(ctx, pl, 8, free_b / 3, true, false, pl->tc));
+    } else if (kernel == 7) {
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
         LNV_TRY(triple_plan_build(ctx, pl, free_b / 3));
@@ -310,6 +322,7 @@ lnv_status plan_set_split(lnv_ctx *ctx, lnv_plan *pl, int on)
 void plan_trim(lnv_plan *plan)
 {
     if (plan->mode != 7) triple_plan_free(&plan->tri);
+    if (plan->mode != 9) group_plan_free(&plan->tc);
     GroupPlan &gp = plan->grp;
     const bool dense = plan->mode == 3 || plan->mode == 5 || plan->mode == 6 || plan->mode == 8,
                sparse = plan->mode == 4;
@@ -333,6 +346,7 @@ void plan_free(lnv_plan *plan)
     cudaFree(plan->items64);
     cudaFree(plan->items128);
     group_plan_free(&plan->grp);
+    group_plan_free(&plan->tc);
     triple_plan_free(&plan->tri);
     delete plan;
 }

@@ -1621,6 +1621,18 @@ template <typename T, int NSF, bool TA, bool TB>
 lnv_status dispatch_mode(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
                          const void *B2, void *C1, void *C2)
 {
+    if (pl->mode == 9) {
+        // tcgen05 tensor cores: one product, FP32 values, NSF = 4, op(B) = B^T;
+        // other cases run the push kernel, which needs no tables
+        if constexpr (NSF == 4 && sizeof(T) == 4 && TB) {
+            LNV_TRY(launch_umma(ctx, pl, A, B1, C1));
+            if (B2) LNV_TRY(launch_umma(ctx, pl, A, B2, C2));
+            return LNV_OK;
+        } else {
+            if (B2) return launch_push2<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, pl->sym1 && pl->split);
+            return launch_push2<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, pl->sym1 && pl->split);
+        }
+    }
     if (pl->mode == 7) {
         if constexpr (NSF == 4) {
             // two fused FP32 products; FP64 runs them one at a time (registers)

@@ -49,6 +49,9 @@ def lib():
                 "lnv_ctx_create": [i32, P, PP],
                 "lnv_ctx_set_stream": [P, P],
                 "lnv_ctx_destroy": [P],
+                "lnv_ctx_device_status": [P],
+                "lnv_ctx_set_wait_limit": [P, ctypes.c_uint64],
+                "lnv_debug_expire_wait": [P],
                 "lnv_pattern_build": [P, P, i64, P, dbl, PP],
                 "lnv_pattern_build_batched": [P, P, i32, P, P, dbl, PP],
                 "lnv_pattern_from_csr": [P, i64, P, P, PP],
@@ -147,6 +150,22 @@ class Context:
     def set_stream(self, stream: torch.cuda.Stream):
         self.stream = stream
         _check(lib().lnv_ctx_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)), "lnv_ctx_set_stream")
+
+    def device_status(self) -> int:
+        """Synchronise the stream; 0, or LNV_ERR_TIMEOUT (-6) if a bounded
+        device-side wait ran out since the last call (the word is cleared)."""
+        return int(lib().lnv_ctx_device_status(self.h))
+
+    def check_device(self):
+        """Raise LnvError if a device-side wait ran out since the last check."""
+        _check(lib().lnv_ctx_device_status(self.h), "device status")
+
+    def set_wait_limit(self, ns: int):
+        _check(lib().lnv_ctx_set_wait_limit(self.h, int(ns)), "lnv_ctx_set_wait_limit")
+
+    def debug_expire_wait(self):
+        """Launch one CTA whose bounded wait runs out (raises the status word)."""
+        _check(lib().lnv_debug_expire_wait(self.h), "lnv_debug_expire_wait")
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
@@ -272,7 +291,7 @@ class Plan:
         self.triples, self.mode = t.value, self.KERNELS[m.value]
 
     KERNELS = ("push", "pull", "pull-merge", "group", "group-sparse", "group-pipe", "group-mma", "triples",
-               "group-pipe-half")
+               "group-pipe-half", "tensor")
 
     def set_kernel(self, kernel):
         k = self.KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)

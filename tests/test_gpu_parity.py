@@ -107,11 +107,23 @@ PRODUCT_CASES = [
     (6.6, 14.6, 8.0, False, False),   # Q = H Z masked
     (8.0, 6.6, 14.6, True, False),    # transposed A, full range
     (6.6, 8.0, 5.0, False, True),     # transposed B, masked
+    (8.0, 21.2, 14.6, False, True),   # Z = L T^T masked (as the evaluation forms it)
 ]
 
 
+def _set_kernel_or_refused(plan, kernel, tb):
+    """Select the kernel; the tensor-core kernel refuses plans without op(B) = B^T."""
+    if kernel == "tensor" and not tb:
+        with pytest.raises(LnvError) as e:
+            plan.set_kernel(kernel)
+        assert e.value.status == -5
+        return False
+    plan.set_kernel(kernel)
+    return True
+
+
 @pytest.mark.parametrize("kernel", ["default", "push", "pull", "pull-merge", "group", "group-sparse",
-                                    "group-pipe", "group-mma", "triples", "group-pipe-half"])
+                                    "group-pipe", "group-mma", "triples", "group-pipe-half", "tensor"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("nsf", [1, 2, 4, 9])
 @pytest.mark.parametrize("case", PRODUCT_CASES)
@@ -126,8 +138,8 @@ def test_masked_product_matches_oracle(ctx, dtype, nsf, case, kernel):
     B = oracle.csr(*ob, rng.standard_normal((ob[1].size, nsf, nsf)))
     A, B = rounded(A, dtype), rounded(B, dtype)
     plan = Plan(ctx, PA, PB, PC, trans_a=ta, trans_b=tb)
-    if kernel != "default":
-        plan.set_kernel(kernel)
+    if kernel != "default" and not _set_kernel_or_refused(plan, kernel, tb):
+        return
     C = plan.multiply(to_dev(A["val"], dtype, ctx.device), to_dev(B["val"], dtype, ctx.device))
     ref = oracle.mprod(oracle.transpose(A) if ta else A, oracle.transpose(B) if tb else B, oc)
     err = rel_fro(C.cpu().numpy(), ref["val"])
@@ -244,6 +256,70 @@ def test_plan_modes_follow_symbolic_counts(ctx):
     assert e.value.status == -5
 
 
+@pytest.mark.parametrize("kernel", ["default", "tensor"])
+@pytest.mark.parametrize("n_atoms", [1, 7, 9, 42, 131])
+def test_transposed_product_ragged_groups(ctx, kernel, n_atoms):
+    """op(B) = B^T products on atom counts that leave a partial last row group
+    (8-row groups of the tensor-core kernel, 4-row groups elsewhere) and
+    partial 32-column tiles, with random clustered positions: FP32 against the
+    oracle."""
+    rng = np.random.default_rng(n_atoms)
+    cell = np.array([20.0, 20.0, 20.0])
+    pos = rng.uniform(0, 9.0, size=(n_atoms, 3))
+    ra, rb, rc = 4.0, 7.0, 6.0
+    PA, PB, PC = (Pattern.build(ctx, pos, cell, r) for r in (ra, rb, rc))
+    oa, ob, oc = (oracle.pattern(pos, cell, r) for r in (ra, rb, rc))
+    A = rounded(oracle.csr(*oa, rng.standard_normal((oa[1].size, 4, 4))), torch.float32)
+    B = rounded(oracle.csr(*ob, rng.standard_normal((ob[1].size, 4, 4))), torch.float32)
+    for ta in (False, True):
+        plan = Plan(ctx, PA, PB, PC, trans_a=ta, trans_b=True)
+        if kernel != "default":
+            plan.set_kernel(kernel)
+        C = plan.multiply(to_dev(A["val"], torch.float32, ctx.device), to_dev(B["val"], torch.float32, ctx.device))
+        ref = oracle.mprod(oracle.transpose(A) if ta else A, oracle.transpose(B), oc)
+        assert rel_fro(C.cpu().numpy(), ref["val"]) <= TOL[torch.float32][0], (ta, plan.mode)
+
+
+def test_tensor_kernel_repeated_calls_are_identical(ctx):
+    """Kernel 9 sums in a fixed order: two launches give bit-identical output."""
+    w, S, H, L = workload(3, 4, 6.6, 8.0, seed=5)
+    pos, cell = w["pos"], w["cell"]
+    PL, PT, PX = (Pattern.build(ctx, pos, cell, r) for r in (8.0, 21.2, 14.6))
+    ot = oracle.pattern(pos, cell, 21.2)
+    T = oracle.csr(*ot, np.random.default_rng(2).standard_normal((ot[1].size, 4, 4)))
+    plan = Plan(ctx, PL, PT, PX, trans_b=True)
+    plan.set_kernel("tensor")
+    Ld, Td = to_dev(L["val"], torch.float32, ctx.device), to_dev(T["val"], torch.float32, ctx.device)
+    c1 = plan.multiply(Ld, Td).cpu().numpy()
+    c2 = plan.multiply(Ld, Td).cpu().numpy()
+    assert np.array_equal(c1, c2)
+    assert ctx.device_status() == 0
+
+
+def test_device_wait_that_runs_out_is_reported(ctx):
+    """A bounded device-side wait that nothing completes gives up after the
+    context's limit and raises LNV_ERR_TIMEOUT on the host; the context stays
+    usable (no fault, no trap)."""
+    assert ctx.device_status() == 0
+    ctx.set_wait_limit(20_000_000)  # 20 ms
+    try:
+        ctx.debug_expire_wait()
+        assert ctx.device_status() == -6
+        assert ctx.device_status() == 0  # cleared by the read
+        with pytest.raises(LnvError) as e:
+            ctx.debug_expire_wait()
+            ctx.check_device()
+        assert e.value.status == -6
+    finally:
+        ctx.set_wait_limit(1_000_000_000)
+    # the context still runs products afterwards
+    pos, cell = synth.si_diamond_positions(2, np.random.default_rng(9))
+    P = Pattern.build(ctx, pos, cell, 6.6)
+    A = torch.ones((P.nnzb, 4, 4), dtype=torch.float32, device=ctx.device)
+    C = Plan(ctx, P, P, P).multiply(A, A)
+    assert torch.isfinite(C).all() and ctx.device_status() == 0
+
+
 def test_product_empty_and_ragged_rows(ctx):
     """Isolated atoms (rows holding only the diagonal) next to a dense cluster."""
     rng = np.random.default_rng(4)
@@ -343,6 +419,31 @@ def test_lnv_4096_atoms_full(ctx, si4096, dtype):
     w, ref = si4096
     _, out, G = _gpu_lnv(ctx, w, dtype)
     _check_lnv(out, G, ref, dtype)
+
+
+@pytest.mark.parametrize("stages", [("Z",), ("W",), ("Z", "W")])
+def test_lnv_512_atoms_tensor_core_products(ctx, si512, stages):
+    """FP32 evaluation with Z = L T^T and / or W = X^T U^T on the tcgen05
+    kernel (9), every output against the FP64 oracle at the FP32 bound."""
+    w, ref = si512
+    sysm = System(ctx, 4, "fp32", w["pos"], w["cell"], 6.6, 8.0)
+    for st in stages:
+        sysm.set_stage_kernel(st, "tensor")
+    assert all(sysm.stage_kernels()[st] == "tensor" for st in stages)
+    _, out, G = _gpu_lnv(ctx, w, torch.float32, sysm=sysm)
+    _check_lnv(out, G, ref, torch.float32)
+    assert ctx.device_status() == 0
+
+
+def test_lnv_4096_atoms_tensor_core_products(ctx, si4096):
+    """The benchmark workload with Z and W on the tcgen05 kernel."""
+    w, ref = si4096
+    sysm = System(ctx, 4, "fp32", w["pos"], w["cell"], 6.6, 8.0)
+    sysm.set_stage_kernel("Z", "tensor")
+    sysm.set_stage_kernel("W", "tensor")
+    _, out, G = _gpu_lnv(ctx, w, torch.float32, sysm=sysm)
+    _check_lnv(out, G, ref, torch.float32)
+    assert ctx.device_status() == 0
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
