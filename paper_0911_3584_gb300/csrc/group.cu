@@ -46,6 +46,35 @@ __global__ void k_bidx(const int64_t *__restrict__ k_off, const int32_t *__restr
     }
 }
 
+// The same table j-major (the tensor-core kernel's form): bidx[j_local][k_local],
+// rows of nk_pad entries (a multiple of 4, so a thread reads the offsets of
+// four consecutive k's in one 8-byte load).
+__global__ void k_bidx_t(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
+                         const int64_t *__restrict__ j_off, const int32_t *__restrict__ j_list,
+                         const int64_t *__restrict__ bidx_off, const int64_t *__restrict__ b_rp,
+                         const int32_t *__restrict__ b_col, int trans_b, uint16_t *bidx)
+{
+    const int64_t g = blockIdx.x;
+    const int64_t kb = k_off[g], nk = k_off[g + 1] - kb;
+    const int64_t jb = j_off[g], nj = j_off[g + 1] - jb;
+    uint16_t *out = bidx + bidx_off[g];
+    const int64_t nk_pad = (nk + 3) & ~int64_t(3);
+    for (int64_t t = threadIdx.x; t < nk * nj; t += blockDim.x) {
+        const int64_t jl = t / nk, kl = t - jl * nk;
+        const int32_t k = k_list[kb + kl], j = j_list[jb + jl];
+        const int32_t row = trans_b ? j : k, key = trans_b ? k : j;
+        int64_t lo = b_rp[row], hi = b_rp[row + 1];
+        const int64_t r0 = lo;
+        while (lo < hi) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            if (b_col[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        const bool found = lo < b_rp[row + 1] && b_col[lo] == key;
+        out[jl * nk_pad + kl] = found ? (uint16_t)(lo - r0) : (uint16_t)0xFFFF;
+    }
+}
+
 // Hit lists: per (group, j) the k's of the group's K with op(B)_kj stored.
 // fill == nullptr: count into cnt[j_entry]; else write hk / hp at hoff.
 __global__ void k_hits(const int64_t *__restrict__ k_off, const int32_t *__restrict__ k_list,
@@ -113,6 +142,7 @@ void group_plan_free(GroupPlan *gp)
     cudaFree(gp->bidx_off); cudaFree(gp->bidx);
     cudaFree(gp->hoff); cudaFree(gp->hk); cudaFree(gp->hp);
     cudaFree(gp->jsplit);
+    cudaFree(gp->items);
     *gp = GroupPlan();
 }
 
@@ -153,12 +183,15 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
             });
         for (auto &x : th) x.join();
     }
+    // the tensor-core kernel's tables: spatial J order, j-major position
+    // table, CTA work items
+    const bool jmajor = &gp == &pl->tc;
     std::vector<int64_t> k_off(ng + 1, 0), j_off(ng + 1, 0), b_off(ng + 1, 0);
     int max_k = 0, max_j = 0;
     for (int64_t g = 0; g < ng; ++g) {
         k_off[g + 1] = k_off[g] + nk[g];
         j_off[g + 1] = j_off[g] + nj[g];
-        b_off[g + 1] = b_off[g] + nk[g] * ((nj[g] + 7) & ~int64_t(7));
+        b_off[g + 1] = b_off[g] + (jmajor ? nj[g] * ((nk[g] + 3) & ~int64_t(3)) : nk[g] * ((nj[g] + 7) & ~int64_t(7)));
         max_k = std::max<int>(max_k, (int)nk[g]);
         max_j = std::max<int>(max_j, (int)nj[g]);
     }
@@ -195,8 +228,26 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
                     // Order J by the set of the group's rows whose C row holds j (then by
                     // index): consecutive columns then need the same rows, so a kernel
                     // can skip the rows that no column of a set keeps.  With a split,
-                    // the columns j >= r0 come first.
-                    {
+                    // the columns j >= r0 come first.  The tensor-core tables order J
+                    // by the atom keys instead (spatially compact column chunks).
+                    if (jmajor) {
+                        const int64_t nj_g = nj[g];
+                        std::vector<int32_t> perm(nj_g);
+                        std::iota(perm.begin(), perm.end(), 0);
+                        const int32_t *jl0 = j_list.data() + j_off[g];
+                        auto key = [&](int32_t jl) -> uint64_t {
+                            return pl->atom_key.empty() ? (uint64_t)jl0[jl] : pl->atom_key[jl0[jl]];
+                        };
+                        std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key(a) < key(b); });
+                        std::vector<int32_t> jl_new(nj_g), cp_new((size_t)nj_g * G);
+                        for (int64_t t = 0; t < nj_g; ++t) {
+                            jl_new[t] = jl0[perm[t]];
+                            for (int m = 0; m < G; ++m)
+                                cp_new[(size_t)t * G + m] = cpos[(size_t)(j_off[g] + perm[t]) * G + m];
+                        }
+                        std::copy(jl_new.begin(), jl_new.end(), j_list.begin() + j_off[g]);
+                        std::copy(cp_new.begin(), cp_new.end(), cpos.begin() + (size_t)j_off[g] * G);
+                    } else {
                         const int64_t nj_g = nj[g];
                         std::vector<int32_t> key(nj_g), perm(nj_g);
                         int64_t n_hi = 0;
@@ -229,6 +280,7 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
     }
     gp.G = G;
     gp.n_groups = ng;
+    gp.jmajor = jmajor ? 1 : 0;
     gp.max_k = max_k;
     gp.max_j = max_j;
     gp.candidates = b_off[ng];
@@ -247,6 +299,24 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
     if (s == LNV_OK) s = upload(j_list, &gp.j_list, &bytes);
     if (s == LNV_OK) s = upload(cpos, &gp.cpos, &bytes);
     if (s == LNV_OK) s = upload(b_off, &gp.bidx_off, &bytes);
+    if (s == LNV_OK && jmajor) {
+        // CTA work items of the tensor-core kernel: (group, first column) per
+        // kTcCols columns of J, ordered by the key of that first column, then
+        // by group, so that the CTAs running at one time cover nearby columns
+        // (and share the rows of op(B) they gather) across many groups
+        std::vector<std::pair<std::pair<uint64_t, int64_t>, int2>> it;
+        for (int64_t g = 0; g < ng; ++g)
+            for (int64_t c0 = 0; c0 < nj[g]; c0 += kTcCols) {
+                const int32_t j = j_list[j_off[g] + c0];
+                const uint64_t key = pl->atom_key.empty() ? (uint64_t)j : pl->atom_key[j];
+                it.push_back({{key, g}, make_int2((int)g, (int)c0)});
+            }
+        std::sort(it.begin(), it.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
+        std::vector<int2> items(it.size());
+        for (size_t q = 0; q < it.size(); ++q) items[q] = it[q].second;
+        gp.n_items = (int64_t)items.size();
+        s = upload(items, &gp.items, &bytes);
+    }
     // hit counts per (group, j) -> offsets of the hit lists
     if (s == LNV_OK && j_off[ng] > 0) {
         int64_t *cnt = nullptr;
@@ -295,8 +365,12 @@ lnv_status group_plan_build_into(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budge
         }
         LNV_CUDA(cudaMalloc(&gp.bidx, need));
         LNV_CUDA(cudaMemsetAsync(gp.bidx, 0xFF, need, ctx->stream));
-        k_bidx<<<(unsigned)ng, 256, 0, ctx->stream>>>(gp.k_off, gp.k_list, gp.j_off, gp.j_list, gp.bidx_off,
-                                                      B->row_ptr, B->col, pl->trans_b, gp.bidx);
+        if (gp.jmajor)
+            k_bidx_t<<<(unsigned)ng, 256, 0, ctx->stream>>>(gp.k_off, gp.k_list, gp.j_off, gp.j_list, gp.bidx_off,
+                                                            B->row_ptr, B->col, pl->trans_b, gp.bidx);
+        else
+            k_bidx<<<(unsigned)ng, 256, 0, ctx->stream>>>(gp.k_off, gp.k_list, gp.j_off, gp.j_list, gp.bidx_off,
+                                                          B->row_ptr, B->col, pl->trans_b, gp.bidx);
         LNV_LAUNCHED();
         LNV_CUDA(cudaStreamSynchronize(ctx->stream));
         gp.bytes += need;

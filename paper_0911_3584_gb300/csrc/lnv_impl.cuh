@@ -112,8 +112,19 @@ struct GroupPlan {
     // multiple of 8), then the rest; jsplit[g] is where the rest starts
     int32_t *jsplit = nullptr;   // [n_groups] or absent
     int max_j_hi = 0, max_j_lo = 0;
+    // the tensor-core kernel's form: J ordered by the plan's atom keys
+    // (spatial order), bidx j-major (bidx[j][k], rows of nk_pad(g) entries, a
+    // multiple of 4) and the CTA work items (group, first column of J) of
+    // kTcCols columns each, sorted by the key of the item's first column
+    int jmajor = 0;
+    int apos_op = 0;             // apos holds op(A)'s stored block (transposed through tr)
+    int2 *items = nullptr;       // [n_items]
+    int64_t n_items = 0;
     size_t bytes = 0;
 };
+
+// Columns j per CTA of the tensor-core kernel (two 128-row tiles of 32 atoms).
+constexpr int kTcCols = 64;
 
 // Triple-list plan of a product (see triples.cu): C's blocks as work items,
 // ordered by groups of 4 rows, then column, then row inside the group; for
@@ -144,6 +155,11 @@ struct lnv_plan {
     GroupPlan grp;
     GroupPlan tc;  // 8-row groups of the tensor-core kernel (9)
     TriplePlan tri;
+    // per-atom ordering keys (spatial, e.g. Morton codes of the positions),
+    // set by the system; empty: the atom index.  Kernel 9 orders each group's
+    // columns and its CTAs by them, so that CTAs running together share rows
+    // of B in L2.
+    std::vector<uint64_t> atom_key;
     // work items (row, first output slot) of the merge-join pull, for 64 and
     // 128 outputs per CTA (device arrays)
     int2 *items64 = nullptr, *items128 = nullptr;
@@ -200,6 +216,8 @@ lnv_status group_plan_build_into(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budge
 // Kernel 9 (umma.cu): C = mask(op(A) B^T) on 8-row groups, tcgen05 tensor
 // cores, FP32 values, NSF = 4.
 lnv_status launch_umma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B, void *C);
+// Finish kernel 9's tables after they are built (op(A) positions for A^T).
+lnv_status umma_prepare(lnv_ctx *ctx, lnv_plan *pl);
 lnv_status scan_exclusive(cudaStream_t st, const int64_t *in, int64_t n, int64_t *out);
 void group_plan_free(GroupPlan *gp);
 // Triple-list plan (triples.cu); LNV_ERR_UNSUPPORTED when it would not fit the budget.

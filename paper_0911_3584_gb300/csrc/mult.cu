@@ -290,6 +290,7 @@ lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
         LNV_TRY(group_plan_build_into(ctx, pl, 8, free_b / 3, true, false, pl->tc));
+        LNV_TRY(umma_prepare(ctx, pl));
     } else if (kernel == 7) {
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;

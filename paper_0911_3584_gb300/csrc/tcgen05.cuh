@@ -63,13 +63,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// Test the phase; if it is not complete the thread may sleep (up to 20 us)
+// until it completes, so waiting warps do not spin on the issue slots.
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(20000)
         : "memory");
     return ok != 0;
 }
@@ -164,16 +166,32 @@ __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
     hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
     lo = x - hi;
 }
-
-// 16-byte global load that does not allocate in L1 (each block is read once
-// per CTA).
-__device__ __forceinline__ float4 ldg_stream(const float *p)
+// The same for two values at once (one packed FP32 subtraction; x - hi is
+// exact, so the rounding mode does not matter).
+__device__ __forceinline__ void split_tf32x2(float x0, float x1, float &h0, float &h1, float &l0, float &l1)
 {
-    float4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p));
-    return v;
+    h0 = __uint_as_float(__float_as_uint(x0) & 0xFFFFE000u);
+    h1 = __uint_as_float(__float_as_uint(x1) & 0xFFFFE000u);
+    unsigned long long x, h, l;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(x0), "f"(x1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(h) : "f"(h0), "f"(h1));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(l) : "l"(x), "l"(h));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l0), "=f"(l1) : "l"(l));
+}
+
+
+// 16-byte asynchronous copy global -> shared (zero-filled when src_bytes = 0),
+// its commit group and wait (up to N groups of this thread still in flight).
+__device__ __forceinline__ void cp_async16(uint32_t dst_smem, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst_smem), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 }  // namespace tc
