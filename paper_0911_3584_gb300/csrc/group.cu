@@ -228,26 +228,9 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
                     // Order J by the set of the group's rows whose C row holds j (then by
                     // index): consecutive columns then need the same rows, so a kernel
                     // can skip the rows that no column of a set keeps.  With a split,
-                    // the columns j >= r0 come first.  The tensor-core tables order J
-                    // by the atom keys instead (spatially compact column chunks).
-                    if (jmajor) {
-                        const int64_t nj_g = nj[g];
-                        std::vector<int32_t> perm(nj_g);
-                        std::iota(perm.begin(), perm.end(), 0);
-                        const int32_t *jl0 = j_list.data() + j_off[g];
-                        auto key = [&](int32_t jl) -> uint64_t {
-                            return pl->atom_key.empty() ? (uint64_t)jl0[jl] : pl->atom_key[jl0[jl]];
-                        };
-                        std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key(a) < key(b); });
-                        std::vector<int32_t> jl_new(nj_g), cp_new((size_t)nj_g * G);
-                        for (int64_t t = 0; t < nj_g; ++t) {
-                            jl_new[t] = jl0[perm[t]];
-                            for (int m = 0; m < G; ++m)
-                                cp_new[(size_t)t * G + m] = cpos[(size_t)(j_off[g] + perm[t]) * G + m];
-                        }
-                        std::copy(jl_new.begin(), jl_new.end(), j_list.begin() + j_off[g]);
-                        std::copy(cp_new.begin(), cp_new.end(), cpos.begin() + (size_t)j_off[g] * G);
-                    } else {
+                    // the columns j >= r0 come first.  The tensor-core tables keep J in
+                    // atom order: with cell-ordered atoms, spatially compact chunks.
+                    if (!jmajor) {
                         const int64_t nj_g = nj[g];
                         std::vector<int32_t> key(nj_g), perm(nj_g);
                         int64_t n_hi = 0;
@@ -301,16 +284,13 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
     if (s == LNV_OK) s = upload(b_off, &gp.bidx_off, &bytes);
     if (s == LNV_OK && jmajor) {
         // CTA work items of the tensor-core kernel: (group, first column) per
-        // kTcCols columns of J, ordered by the key of that first column, then
-        // by group, so that the CTAs running at one time cover nearby columns
+        // kTcCols columns of J, ordered by that first column's atom, then by
+        // group, so that the CTAs running at one time cover nearby columns
         // (and share the rows of op(B) they gather) across many groups
         std::vector<std::pair<std::pair<uint64_t, int64_t>, int2>> it;
         for (int64_t g = 0; g < ng; ++g)
-            for (int64_t c0 = 0; c0 < nj[g]; c0 += kTcCols) {
-                const int32_t j = j_list[j_off[g] + c0];
-                const uint64_t key = pl->atom_key.empty() ? (uint64_t)j : pl->atom_key[j];
-                it.push_back({{key, g}, make_int2((int)g, (int)c0)});
-            }
+            for (int64_t c0 = 0; c0 < nj[g]; c0 += kTcCols)
+                it.push_back({{(uint64_t)j_list[j_off[g] + c0], g}, make_int2((int)g, (int)c0)});
         std::sort(it.begin(), it.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
         std::vector<int2> items(it.size());
         for (size_t q = 0; q < it.size(); ++q) items[q] = it[q].second;

@@ -112,8 +112,8 @@ struct GroupPlan {
     // multiple of 8), then the rest; jsplit[g] is where the rest starts
     int32_t *jsplit = nullptr;   // [n_groups] or absent
     int max_j_hi = 0, max_j_lo = 0;
-    // the tensor-core kernel's form: J ordered by the plan's atom keys
-    // (spatial order), bidx j-major (bidx[j][k], rows of nk_pad(g) entries, a
+    // the tensor-core kernel's form: J in atom order (spatial order for
+    // cell-ordered atoms), bidx j-major (bidx[j][k], rows of nk_pad(g) entries, a
     // multiple of 4) and the CTA work items (group, first column of J) of
     // kTcCols columns each, sorted by the key of the item's first column
     int jmajor = 0;
@@ -155,11 +155,6 @@ struct lnv_plan {
     GroupPlan grp;
     GroupPlan tc;  // 8-row groups of the tensor-core kernel (9)
     TriplePlan tri;
-    // per-atom ordering keys (spatial, e.g. Morton codes of the positions),
-    // set by the system; empty: the atom index.  Kernel 9 orders each group's
-    // columns and its CTAs by them, so that CTAs running together share rows
-    // of B in L2.
-    std::vector<uint64_t> atom_key;
     // work items (row, first output slot) of the merge-join pull, for 64 and
     // 128 outputs per CTA (device arrays)
     int2 *items64 = nullptr, *items128 = nullptr;
