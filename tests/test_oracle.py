@@ -463,3 +463,48 @@ def test_truncation_error_shrinks_with_the_ranges():
     assert np.all(np.diff(errs[:-1, 2]) < 0)
     assert np.all(errs[-1] < 1e-12)
     assert errs[0, 2] > 1e-6  # the truncation is really felt
+
+
+@pytest.mark.parametrize("nsf", [2, 4])
+@pytest.mark.parametrize("r_x,r_t", [(5.0, 6.0), (6.0, 8.0)])
+def test_truncated_oracle_against_dense_masked_definition(nsf, r_x, r_t):
+    """The truncated evaluation written out densely with 0/1 block masks on a
+    64-atom system, at ranges below the exact ones (R_X = 7.5, R_T = 10.5)
+    where T = SX is not symmetric, so the association matters:
+      X = M_rx o (L S), Y = M_rx o (L H), T = M_rt o (S X), U = M_rt o (S Y),
+      Z = M_rx o (L T^T), Q = M_L o (H Z), W = M_L o (X^T U^T) taken on the
+      block upper triangle (j >= i) and mirrored below it,
+      E = 2 (3 Tr[XY] - 2 Tr[ZY]), N_e = 2 (3 Tr[XX] - 2 Tr[ZX]),
+      G = M_L o (6 (U + U^T) - 4 (Q^T + W + Q)).
+    Z from T instead of T^T, or W mirrored from the other triangle, fails."""
+    w, S, H, L = _si(2, nsf, 3.0, 4.5, seed=11)
+    pos, cell = w["pos"], w["cell"]
+    n = pos.shape[0]
+    Sd, Hd, Ld = (to_dense(M["rp"], M["col"], M["val"]) for M in (S, H, L))
+    Mx = mask_dense(*oracle.pattern(pos, cell, r_x), nsf)
+    Mt = mask_dense(*oracle.pattern(pos, cell, r_t), nsf)
+    Ml = mask_dense(L["rp"], L["col"], nsf)
+    X, Y = Mx * (Ld @ Sd), Mx * (Ld @ Hd)
+    T, U = Mt * (Sd @ X), Mt * (Sd @ Y)
+    assert np.linalg.norm(T - T.T) > 1e-5 * np.linalg.norm(T)  # the association is felt
+    Z = Mx * (Ld @ T.T)
+    E = 2 * (3 * np.trace(X @ Y) - 2 * np.trace(Z @ Y))
+    Ne = 2 * (3 * np.trace(X @ X) - 2 * np.trace(Z @ X))
+    Q = Ml * (Hd @ Z)
+    W = Ml * (X.T @ U.T)
+    blk = np.kron(np.arange(n)[:, None] <= np.arange(n)[None, :], np.ones((nsf, nsf)))    # j >= i
+    strict = np.kron(np.arange(n)[:, None] < np.arange(n)[None, :], np.ones((nsf, nsf)))  # j > i
+    Wm = blk * W + (strict * W).T
+    Gd = Ml * (6 * (U + U.T) - 4 * (Q.T + Wm + Q))
+    tr = oracle.lnv_energy_grad_truncated(pos, cell, 3.0, 4.5, r_x, r_t, S, H, L)
+    assert tr["E"] == pytest.approx(E, rel=1e-12)
+    assert tr["Ne"] == pytest.approx(Ne, rel=1e-12)
+    G = from_dense(Gd, L["rp"], L["col"], nsf)
+    assert np.linalg.norm(tr["G"] - G) <= 1e-12 * np.linalg.norm(G)
+    # the plausible slips the pin guards against are far off
+    Z_bad = Mx * (Ld @ T)
+    E_bad = 2 * (3 * np.trace(X @ Y) - 2 * np.trace(Z_bad @ Y))
+    assert abs(E_bad - E) > 1e-9 * abs(E)
+    W_bad = blk.T * W + (strict.T * W).T
+    G_bad = from_dense(Ml * (6 * (U + U.T) - 4 * (Q.T + W_bad + Q)), L["rp"], L["col"], nsf)
+    assert np.linalg.norm(G_bad - G) > 1e-6 * np.linalg.norm(G)
