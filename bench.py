@@ -247,7 +247,40 @@ def time_path(ctx, w, prec, steps, warmup, dist, kernels=None):
     return res
 
 
-def roofline(res):
+def measured_peaks():
+    """The machine's measured peaks (generated MEASURED_PEAKS.json at the repo
+    root), or the profiling recipe's fallback figures."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"bf16_tflops": float(d["bf16_tflops"]), "hbm_gbs": float(d["hbm_gbs"]), "source": "of measured"}
+    except (OSError, KeyError, ValueError):
+        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0, "source": "of fallback"}
+
+
+def roofline_tensor(res):
+    """Stages on the tcgen05 kernel: algorithmic flops (one pass, unpadded
+    blocks) per stage time against the dense TF32 tensor peak, taken as half
+    the measured BF16 burst peak (the nominal TF32 : BF16 ratio); the kernel
+    issues three TF32 passes (hi*hi, hi*lo, lo*hi) on dense 8-row tiles."""
+    pk = measured_peaks()
+    tf32 = pk["bf16_tflops"] / 2.0
+    out = []
+    for st, k in res["kernels"].items():
+        if k != "tensor" or res["stage_ms"].get(st, 0) <= 0:
+            continue
+        ms = res["stage_ms"][st]
+        achieved = res["flops_stage"][st] / (ms * 1e-3) / 1e12
+        out.append({"stage": st, "kernel": f"{KERNEL_NAME[k]} ({STAGE_KERNEL[st]})", "bound": "tensor",
+                    "achieved": round(achieved, 3), "peak": round(tf32, 1), "unit": "TFLOP/s",
+                    "frac": round(achieved / tf32, 4), "kernel_ms": round(ms, 4),
+                    "algorithmic_flops_per_launch": res["flops_stage"][st],
+                    "peak_source": f"dense TF32 = measured BF16 burst / 2 ({pk['source']})"})
+    return out
+
+
+def roofline(res, fma_tflops=None):
     prec = res["prec"]
     # dominant product kernel by measured time
     cand = {k: v for k, v in res["stage_ms"].items() if k in STAGE_KERNEL and v > 0}
@@ -264,7 +297,9 @@ def roofline(res):
             "stage": stage, "kernel_ms": round(ms, 4),
             "algorithmic_flops_per_launch": res["flops_stage"][stage],
             "peak_source": ("derived: 152 SMs x 2.07 GHz x 256 flop/clk/SM (FP32 FMA)" if prec == "fp32"
-                            else "nominal GB300 FP64 rate 1.25 TFLOP/s")}
+                            else "nominal GB300 FP64 rate 1.25 TFLOP/s"),
+            "peak_fma_probe": round(fma_tflops, 3) if fma_tflops else None,
+            "frac_of_fma_probe": round(achieved / fma_tflops, 4) if fma_tflops else None}
 
 
 def e2e(ctx, res, steps, warmup):
@@ -409,6 +444,10 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# wall-clock windows of the timed loops of a configuration run (for its clock record)
+_TIMED = []
+
+
 def _flush_timed(ctx, fn, steps, warmup):
     """CUDA-event time of `steps` calls of fn (L2 flushed before each, outside
     the events), after `warmup` calls; returns seconds."""
@@ -417,6 +456,7 @@ def _flush_timed(ctx, fn, steps, warmup):
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
+    _TIMED.append([time.time(), None])
     total = 0.0
     for _ in range(steps):
         flush.zero_()
@@ -426,6 +466,7 @@ def _flush_timed(ctx, fn, steps, warmup):
         b.record(ctx.stream)
         torch.cuda.synchronize()
         total += a.elapsed_time(b) / 1e3
+    _TIMED[-1][1] = time.time()
     return total
 
 
@@ -505,7 +546,7 @@ def run_batch64(args, ctx):
                 "value": round(n_s / t_s, 3), "unit": "atoms/s", "cores": oracle.num_threads(),
                 "kind": "oracle", "sample": f"full FP64 evaluations of the batch's systems of at most 4^3 cells "
                                             f"({n_s} atoms, {t_s:.1f} s)"}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_large(args, ctx, nsf, r_l, autograd):
@@ -562,7 +603,7 @@ def run_large(args, ctx, nsf, r_l, autograd):
         "memory": {"library_workspace_bytes": sysm.workspace_size(True),
                    "torch_peak_bytes_during_steps": int(peak), "torch_bytes_before_steps": int(base_alloc)},
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_minimize(args, ctx, prec):
@@ -588,6 +629,7 @@ def run_minimize(args, ctx, prec):
     iters, hist = sysm.minimize(S, H, Lw, mu, max_iter=args.steps, tol=1e-30)
     torch.cuda.synchronize()
     dt = time.time() - t0
+    _TIMED.append([t0, t0 + dt])
     n = w["pos"].shape[0]
     line = {
         "metric": "atoms/s per LNV conjugate-gradient iteration (3 evaluations)",
@@ -601,7 +643,7 @@ def run_minimize(args, ctx, prec):
         "omega": {"start": float(hist[0, 0]), "end": float(hist[-1, 0])},
         "grad_rms": {"start": float(hist[0, 3]), "end": float(hist[-1, 3])},
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_truncation(args, ctx):
@@ -642,7 +684,7 @@ def run_truncation(args, ctx):
                    "truncation rows: errors against the exact FP64 evaluation"},
         "truncation": rows,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -667,23 +709,36 @@ def main():
         dist = tdist
     dev = torch.device("cuda", local)
     ctx = Context(dev)
-    if args.config != "si4096":
-        if args.config == "batch64":
-            run_batch64(args, ctx)
-        elif args.config == "si32768_nsf9":
-            run_large(args, ctx, 9, 10.0, False)
-        elif args.config == "si4096_truncation":
-            run_truncation(args, ctx)
-        elif args.config == "si4096_minimize":
-            run_minimize(args, ctx, "fp32")
-        elif args.config == "si4096_minimize_fp64":
-            run_minimize(args, ctx, "fp64")
-        else:
-            run_large(args, ctx, 4, 10.0, True)
-        return
-    w, _ = build_inputs(ctx, torch.float64)
     props = torch.cuda.get_device_properties(dev)
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
+    if args.config != "si4096":
+        # every configuration line carries the clock record of its run
+        clocks = Clocks(gpu_id)
+        clocks.start()
+        t0 = time.time()
+        if args.config == "batch64":
+            line = run_batch64(args, ctx)
+        elif args.config == "si32768_nsf9":
+            line = run_large(args, ctx, 9, 10.0, False)
+        elif args.config == "si4096_truncation":
+            line = run_truncation(args, ctx)
+        elif args.config == "si4096_minimize":
+            line = run_minimize(args, ctx, "fp32")
+        elif args.config == "si4096_minimize_fp64":
+            line = run_minimize(args, ctx, "fp64")
+        else:
+            line = run_large(args, ctx, 4, 10.0, True)
+        clocks.stop()
+        # clocks during the timed loops (the whole run if none was recorded)
+        win = [w_ for w_ in _TIMED if w_[1] is not None]
+        line["clocks"] = clocks.summary(min(w_[0] for w_ in win), max(w_[1] for w_ in win)) if win \
+            else clocks.summary(t0, time.time())
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+    w, _ = build_inputs(ctx, torch.float64)
+    # measured FMA-pipe rates (the SIMT products' measured ALU roofline)
+    fma = {p_: ctx.fma_rate(p_) for p_ in ("fp32", "fp64")}
     clocks = Clocks(gpu_id)
     clocks.start()
     r32 = time_path(ctx, w, "fp32", args.steps, args.warmup, dist, pinned(args.kernels, "fp32"))
@@ -707,12 +762,14 @@ def main():
                    "l2": "flushed between timed steps (256 MB write, outside the timed events)",
                    "parallelism": f"replicas x{world} (independent systems)"},
         "gflops": round(r32["flops"] / (r32["ms_per_step"] * 1e-3) / 1e9, 1),
-        "roofline": roofline(r32),
+        "roofline": roofline(r32, fma["fp32"]),
+        "roofline_tensor_stages": roofline_tensor(r32),
         "e2e": e2e32,
         "gpu_launches": r32["launches"],
         "stage_ms": {k: round(v, 4) for k, v in r32["stage_ms"].items()},
         "stage_kernels": r32["kernels"],
         "t_mirrored": r32["t_mirrored"],
+        "fma_probe_tflops": {k: round(v, 3) for k, v in fma.items()},
         "setup": dict(r32["setup"], note="patterns, plans and tables (system_s) and the autotuner "
                                           "(autotune_s), outside the timed steps"),
     }
@@ -723,7 +780,7 @@ def main():
         line["fp64"] = {"value": round(v64, 1), "unit": "atoms/s",
                         "ms_per_step": round(t64 * 1e3 / args.steps, 4),
                         "gflops": round(r64["flops"] / (r64["ms_per_step"] * 1e-3) / 1e9, 1),
-                        "roofline": roofline(r64), "gpu_launches": r64["launches"],
+                        "roofline": roofline(r64, fma["fp64"]), "gpu_launches": r64["launches"],
                         "stage_ms": {k: round(v, 4) for k, v in r64["stage_ms"].items()},
                         "stage_kernels": r64["kernels"], "t_mirrored": r64["t_mirrored"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -99,6 +99,14 @@ int64_t lnv_launch_count(void);
  * wait in nanoseconds (default 1 s; > 0). */
 lnv_status lnv_ctx_device_status(lnv_ctx *ctx);
 lnv_status lnv_ctx_set_wait_limit(lnv_ctx *ctx, uint64_t ns);
+/* Measured rate of the fused multiply-add pipe of the context's GPU in the
+ * given precision (TFLOP/s, 2 flop per FMA): eight independent FMA chains per
+ * thread, eight 256-thread CTAs per SM, best of three timed launches.  The
+ * SIMT block products (Sec. 3: the main load is sparse matrix
+ * multiplication) are bound by this pipe; it is the measured denominator of
+ * their rooflines beside the nominal one.  Allocates a small buffer and
+ * synchronises. */
+lnv_status lnv_probe_fma_rate(lnv_ctx *ctx, lnv_prec prec, double *tflops);
 /* Exercise the bounded-wait path: one CTA waits on a barrier that nothing
  * completes, gives up after the context's wait limit and raises the status
  * word (no fault, no trap).  Asynchronous; read the result with
@@ -216,12 +224,14 @@ lnv_status lnv_trace_product(lnv_ctx *ctx, const lnv_pattern *P, int nsf, lnv_pr
  * buffer.  The paper has no counterpart; this is a library convenience.
  * The per-row partial sums live in a static device array of 262144 doubles
  * (2 MiB) that every GPU loading the library keeps until exit; patterns with
- * more rows fail with LNV_ERR_UNSUPPORTED.  The call allocates nothing.  Its
- * first call on a device looks the array's address up (cudaGetSymbolAddress)
- * and caches it: make that first call before any stream capture.  All calls
- * on a device share the array, so calls whose kernels overlap on the GPU
- * race; serialise them.  Every row's partial sum is written before it is
- * read, so the array needs no clearing between calls. */
+ * more rows fail with LNV_ERR_UNSUPPORTED.  The call allocates nothing.  It
+ * looks the array's device address up (cudaGetSymbolAddress) on every call
+ * made outside a stream capture, so the address stays right after a
+ * cudaDeviceReset, and keeps the last one for calls made during a capture:
+ * make one call on the device before capturing.  All calls on a device share
+ * the array, so calls whose kernels overlap on the GPU race; serialise them.
+ * Every row's partial sum is written before it is read, so the array needs no
+ * clearing between calls. */
 lnv_status lnv_trace_product_noalloc(lnv_ctx *ctx, const lnv_pattern *P, int nsf,
                                      lnv_prec prec, const void *A_dev, const void *B_dev,
                                      double *out_dev);

@@ -28,10 +28,13 @@ static __device__ __align__(256) double g_trace_scratch[kNoAllocMaxRows];
 std::mutex g_scratch_mu;
 double *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_trace_scratch on the current device (ctx->device),
-// looked up once per device.  In host code the array's name is only a
-// host-side stand-in and must never be passed to a kernel.
-lnv_status scratch_address(int device, double **out)
+// Device address of g_trace_scratch on the current device (ctx->device).  In
+// host code the array's name is only a host-side stand-in and must never be
+// passed to a kernel.  The address is looked up again on every call made
+// outside a stream capture (so it stays right after cudaDeviceReset, which
+// gives the array a new address in the new context) and cached for calls
+// made during a capture, where the lookup is not allowed.
+lnv_status scratch_address(int device, bool refresh, double **out)
 {
     if (device < 0 || device >= kMaxDevices) {
         lnv::set_error("device index %d is beyond the %d devices this entry point supports",
@@ -39,7 +42,7 @@ lnv_status scratch_address(int device, double **out)
         return LNV_ERR_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[device]) {
+    if (refresh || !g_scratch_addr[device]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_trace_scratch);
         if (e != cudaSuccess || !p) {
@@ -68,8 +71,10 @@ extern "C" lnv_status lnv_trace_product_noalloc(lnv_ctx *ctx, const lnv_pattern 
         return LNV_ERR_UNSUPPORTED;
     }
     LNV_CUDA(cudaSetDevice(ctx->device));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LNV_CUDA(cudaStreamIsCapturing(ctx->stream, &cs));
     double *scratch = nullptr;
-    LNV_TRY(scratch_address(ctx->device, &scratch));
+    LNV_TRY(scratch_address(ctx->device, cs == cudaStreamCaptureStatusNone, &scratch));
     const void *A[1] = {A_dev}, *B[1] = {B_dev};
     LNV_TRY(lnv::trace_rows(ctx, P, nsf, prec, 1, A, B, scratch));
     return lnv::reduce_rows(ctx, scratch, P->n, 1, 1, nullptr, out_dev, 1, 0);

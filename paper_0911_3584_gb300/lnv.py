@@ -52,6 +52,7 @@ def lib():
                 "lnv_ctx_device_status": [P],
                 "lnv_ctx_set_wait_limit": [P, ctypes.c_uint64],
                 "lnv_debug_expire_wait": [P],
+                "lnv_probe_fma_rate": [P, i32, P],
                 "lnv_pattern_build": [P, P, i64, P, dbl, PP],
                 "lnv_pattern_build_batched": [P, P, i32, P, P, dbl, PP],
                 "lnv_pattern_from_csr": [P, i64, P, P, PP],
@@ -162,6 +163,13 @@ class Context:
 
     def set_wait_limit(self, ns: int):
         _check(lib().lnv_ctx_set_wait_limit(self.h, int(ns)), "lnv_ctx_set_wait_limit")
+
+    def fma_rate(self, prec: str) -> float:
+        """Measured FMA-pipe rate of this GPU in TFLOP/s ("fp32" or "fp64")."""
+        v = ctypes.c_double()
+        _check(lib().lnv_probe_fma_rate(self.h, 0 if prec == "fp64" else 1, ctypes.byref(v)),
+               "lnv_probe_fma_rate")
+        return float(v.value)
 
     def debug_expire_wait(self):
         """Launch one CTA whose bounded wait runs out (raises the status word)."""
