@@ -459,14 +459,15 @@ def test_lnv_4096_atoms_bench_configuration(ctx, si4096, dtype):
     _check_lnv(out, G, ref, dtype)
 
 
-@pytest.mark.parametrize("nsf", [4, pytest.param(9, marks=pytest.mark.skipif(
-    os.environ.get("LNV_FULL_SIZE_TESTS") != "1",
-    reason="NSF = 9 at 32768 atoms: set LNV_FULL_SIZE_TESTS=1 (16 GB of host memory; not yet run on a GPU)"))])
+@pytest.mark.parametrize("nsf", [4, 9])
 def test_32768_atoms_sampled_rows_bench_configuration(ctx, nsf):
     """The 16x16x16-cell workloads (32768 atoms, R_SH = 6.6 A, R_L = 10 A,
     NSF = 4 and 9) in the configuration bench.py times them (FP32, autotuned):
     dE/dL and dN_e/dL on the rows of three atoms against the row-chain oracle
-    (oracle/sampled.py), which forms those rows from the definition."""
+    (oracle/sampled.py), which forms those rows from the definition.  With
+    NSF = 4, E and N_e are also checked against an FP64 evaluation of the same
+    system on the GPU, at the FP32 bound (2e-5 relative); at NSF = 9 the FP64
+    intermediates (about 160 GB) are not formed."""
     from oracle.sampled import lnv_grad_rows
 
     w = synth.si_workload(16, nsf, 6.6, 10.0, 0, oracle.pattern)
@@ -483,6 +484,16 @@ def test_32768_atoms_sampled_rows_bench_configuration(ctx, nsf):
     gn = GN.double().cpu().numpy()[ref["pos"]]
     assert rel_fro(g, ref["G"]) <= TOL[torch.float32][0]
     assert rel_fro(gn, ref["GN"]) <= TOL[torch.float32][0]
+    if nsf == 4:
+        o32 = out.cpu().numpy()[0]
+        del sysm, G, GN, out
+        torch.cuda.empty_cache()
+        s64 = System(ctx, nsf, "fp64", w["pos"], w["cell"], 6.6, 10.0)
+        # the FP64 evaluation of the same (FP32-rounded) inputs
+        o64, _ = s64.energy_grad(Sd.double(), Hd.double(), Ld.double(), grad=False)
+        o64 = o64.cpu().numpy()[0]
+        assert abs(o32[0] - o64[0]) <= TOL[torch.float32][1] * abs(o64[0]), (o32[0], o64[0])
+        assert abs(o32[1] - o64[1]) <= TOL[torch.float32][1] * abs(o64[1]), (o32[1], o64[1])
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
