@@ -140,7 +140,7 @@ class Clocks:
 
 def product_source_sha():
     h = hashlib.sha1()
-    for f in ("mult_kernels.cuh", "mult.cu"):
+    for f in ("mult_kernels.cuh", "mult.cu", "umma.cu", "tcgen05.cuh", "group.cu"):
         with open(os.path.join(ROOT, "paper_0911_3584_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -274,7 +274,8 @@ def roofline_tensor(res):
         achieved = res["flops_stage"][st] / (ms * 1e-3) / 1e12
         out.append({"stage": st, "kernel": f"{KERNEL_NAME[k]} ({STAGE_KERNEL[st]})", "bound": "tensor",
                     "achieved": round(achieved, 3), "peak": round(tf32, 1), "unit": "TFLOP/s",
-                    "frac": round(achieved / tf32, 4), "kernel_ms": round(ms, 4),
+                    "frac": round(achieved / tf32, 4), "traffic": ncu_traffic(st, res["prec"]),
+                    "kernel_ms": round(ms, 4),
                     "algorithmic_flops_per_launch": res["flops_stage"][st],
                     "peak_source": f"dense TF32 = measured BF16 burst / 2 ({pk['source']})"})
     return out

@@ -320,6 +320,33 @@ def test_device_wait_that_runs_out_is_reported(ctx):
     assert torch.isfinite(C).all() and ctx.device_status() == 0
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("kernel", ["default", "tensor"])
+def test_multiply_alpha_beta(ctx, dtype, kernel):
+    """lnv_bsr_multiply's C = alpha mask(op(A) op(B)) + beta C through the C
+    ABI: beta = 0 overwrites C without reading it (NaN there does not leak),
+    beta != 0 combines with the old C; against the oracle's product."""
+    rng = np.random.default_rng(41)
+    pos, cell = synth.si_diamond_positions(3, rng)
+    PA, PB, PC = (Pattern.build(ctx, pos, cell, r) for r in (8.0, 21.2, 14.6))
+    oa, ob, oc = (oracle.pattern(pos, cell, r) for r in (8.0, 21.2, 14.6))
+    A = rounded(oracle.csr(*oa, rng.standard_normal((oa[1].size, 4, 4))), dtype)
+    B = rounded(oracle.csr(*ob, rng.standard_normal((ob[1].size, 4, 4))), dtype)
+    C0 = rounded(oracle.csr(*oc, rng.standard_normal((oc[1].size, 4, 4))), dtype)
+    plan = Plan(ctx, PA, PB, PC, trans_b=True)
+    if kernel != "default":
+        plan.set_kernel(kernel)
+    P = oracle.mprod(A, oracle.transpose(B), oc)["val"]
+    Ad, Bd = to_dev(A["val"], dtype, ctx.device), to_dev(B["val"], dtype, ctx.device)
+    for alpha, beta in [(1.0, 0.0), (0.5, 0.0), (0.5, -2.0), (-1.25, 1.0), (0.0, 3.0)]:
+        C = to_dev(C0["val"], dtype, ctx.device)
+        if beta == 0.0:
+            C.fill_(float("nan"))
+        plan.multiply(Ad, Bd, C, alpha=alpha, beta=beta)
+        ref = alpha * P + (beta * C0["val"] if beta != 0.0 else 0.0)
+        assert rel_fro(C.cpu().numpy(), ref) <= TOL[dtype][0], (alpha, beta)
+
+
 def test_product_empty_and_ragged_rows(ctx):
     """Isolated atoms (rows holding only the diagonal) next to a dense cluster."""
     rng = np.random.default_rng(4)
