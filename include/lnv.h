@@ -203,11 +203,18 @@ lnv_status lnv_plan_info(const lnv_plan *plan, int64_t *triples, int *mode);
 lnv_status lnv_plan_set_kernel(lnv_ctx *ctx, lnv_plan *plan, int kernel);
 lnv_status lnv_plan_destroy(lnv_plan *plan);
 
-/* Numeric product on the context stream.  A_dev, B_dev, C_dev are value
- * arrays in `prec` (double or float) with NSF x NSF blocks; C is
- * overwritten.  NSF in {1, 2, 4, 9}. */
+/* Numeric product on the context stream (Sec. 2 operation (i), the sparse
+ * matrix multiplication of Sec. 3): C = alpha mask_C(op(A) op(B)) + beta C.
+ * A_dev, B_dev, C_dev are value arrays in `prec` (double or float) with
+ * NSF x NSF blocks, NSF in {1, 2, 4, 9}.  beta = 0: C is overwritten (its
+ * old values are not read, NaN included) and nothing is allocated.  beta !=
+ * 0: the product is formed in a scratch buffer the context keeps (allocated
+ * or grown on the first such call, which then synchronises; later calls of
+ * the same size allocate nothing) and combined with C elementwise in FP64
+ * arithmetic, rounded to the value precision. */
 lnv_status lnv_bsr_multiply(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec,
-                            const void *A_dev, const void *B_dev, void *C_dev);
+                            const void *A_dev, const void *B_dev, void *C_dev, double alpha,
+                            double beta);
 
 /* ---- a4: traces (N_e = 2 Tr[KS], Sec. 2; E = 2 Tr[KH]) ----------------- */
 

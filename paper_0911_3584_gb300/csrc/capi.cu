@@ -225,6 +225,7 @@ lnv_status lnv_ctx_destroy(lnv_ctx *ctx)
 {
     if (ctx) {
         cudaFree(ctx->scratch);
+        cudaFree(ctx->prod_scratch);
         cudaFree(ctx->dev_status);
     }
     delete ctx;
@@ -336,11 +337,29 @@ lnv_status lnv_plan_destroy(lnv_plan *plan)
 }
 
 lnv_status lnv_bsr_multiply(lnv_ctx *ctx, const lnv_plan *plan, int nsf, lnv_prec prec,
-                            const void *A_dev, const void *B_dev, void *C_dev)
+                            const void *A_dev, const void *B_dev, void *C_dev, double alpha, double beta)
 {
     LNV_TRY(set_dev(ctx));
+    LNV_ARG(plan, "null plan");
     LNV_ARG(aligned16(A_dev) && aligned16(B_dev) && aligned16(C_dev), "value arrays must be 16-byte aligned");
-    return multiply(ctx, plan, nsf, prec, A_dev, B_dev, C_dev);
+    LNV_ARG(prec == LNV_FP64 || prec == LNV_FP32, "unknown precision");
+    const int64_t n = plan->C->nnzb * (int64_t)nsf * nsf;
+    if (beta == 0.0) {
+        LNV_TRY(multiply(ctx, plan, nsf, prec, A_dev, B_dev, C_dev));
+        if (alpha != 1.0) LNV_TRY(vec_axpby(ctx, prec, n, alpha, C_dev, 0.0, nullptr, C_dev));
+        return LNV_OK;
+    }
+    const size_t bytes = (size_t)std::max<int64_t>(n, 1) * elem_size(prec);
+    if (ctx->prod_scratch_bytes < bytes) {
+        LNV_CUDA(cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->prod_scratch);
+        ctx->prod_scratch = nullptr;
+        ctx->prod_scratch_bytes = 0;
+        LNV_CUDA(cudaMalloc(&ctx->prod_scratch, bytes));
+        ctx->prod_scratch_bytes = bytes;
+    }
+    LNV_TRY(multiply(ctx, plan, nsf, prec, A_dev, B_dev, ctx->prod_scratch));
+    return vec_axpby(ctx, prec, n, alpha, ctx->prod_scratch, beta, C_dev, C_dev);
 }
 
 lnv_status lnv_trace_product(lnv_ctx *ctx, const lnv_pattern *P, int nsf, lnv_prec prec,

@@ -69,6 +69,8 @@ struct lnv_ctx {
     unsigned long long wait_ns = 1000000000ull;  // limit of one device-side wait
     double *scratch = nullptr;  // reduction partials of lnv_vec_dot (grown on demand)
     size_t scratch_n = 0;
+    void *prod_scratch = nullptr;  // product of lnv_bsr_multiply with beta != 0 (grown on demand)
+    size_t prod_scratch_bytes = 0;
 };
 
 struct lnv_pattern {

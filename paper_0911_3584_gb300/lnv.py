@@ -62,7 +62,7 @@ def lib():
                 "lnv_plan_info": [P, P, P],
                 "lnv_plan_set_kernel": [P, P, i32],
                 "lnv_plan_destroy": [P],
-                "lnv_bsr_multiply": [P, P, i32, i32, P, P, P],
+                "lnv_bsr_multiply": [P, P, i32, i32, P, P, P, dbl, dbl],
                 "lnv_trace_product": [P, P, i32, i32, P, P, P, P],
                 "lnv_system_create": [P, i32, i32, P, i64, i32, P, P, dbl, dbl, PP],
                 "lnv_system_create_truncated": [P, i32, i32, P, i64, i32, P, P, dbl, dbl, dbl, dbl, PP],
@@ -306,15 +306,19 @@ class Plan:
         _check(lib().lnv_plan_set_kernel(self.ctx.h, self.h, k), "lnv_plan_set_kernel")
         self.mode = self.KERNELS[k]
 
-    def multiply(self, A_vals, B_vals, C_vals=None, nsf=None, prec=None):
+    def multiply(self, A_vals, B_vals, C_vals=None, nsf=None, prec=None, alpha=1.0, beta=0.0):
+        """C = alpha mask_C(op(A) op(B)) + beta C (C is overwritten when beta = 0)."""
         nsf = nsf or A_vals.shape[-1]
         prec = PREC[prec] if prec is not None else (FP64 if A_vals.dtype == torch.float64 else FP32)
         if C_vals is None:
+            if beta != 0.0:
+                raise ValueError("beta != 0 needs C_vals")
             C_vals = torch.empty((self.C.nnzb, nsf, nsf), dtype=DTYPE[prec], device=self.ctx.device)
         a = _vals(A_vals, self.A, nsf, prec, "A")
         b = _vals(B_vals, self.B, nsf, prec, "B")
         c = _vals(C_vals, self.C, nsf, prec, "C")
-        _check(lib().lnv_bsr_multiply(self.ctx.h, self.h, nsf, prec, a, b, c), "lnv_bsr_multiply")
+        _check(lib().lnv_bsr_multiply(self.ctx.h, self.h, nsf, prec, a, b, c, float(alpha), float(beta)),
+               "lnv_bsr_multiply")
         return C_vals
 
     def __del__(self):
