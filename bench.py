@@ -471,23 +471,46 @@ def _flush_timed(ctx, fn, steps, warmup):
     return total
 
 
-def run_batch64(args, ctx):
+def run_batch64(args, ctx, dist=None):
     """64 independent Si supercells (n^3 cells, n uniform in 2..10, seeds
     1000+s) evaluated together: one block-diagonal system, autotuned, one CUDA
-    graph replay per step; against per-system launches of the same systems."""
+    graph replay per step; against per-system launches of the same systems.
+    Over N ranks, whole systems go to ranks by their exact block-triple counts
+    (longest processing time first); each rank evaluates its own systems and
+    the job time is the slowest rank's."""
     import gc
 
     import torch
 
     import synth
     from paper_0911_3584_gb300 import Pattern, System
+    from paper_0911_3584_gb300.shard import assign_lpt, lpt_loads
 
     def pattern_fn(pos, cell, R):
         P = Pattern.build(ctx, pos, cell, R)
         return P.row_ptr.cpu().numpy(), P.col.cpu().numpy()
 
-    counts = synth.batch_cell_counts(64, 2, 10, 0)
-    ws = [synth.si_workload(n, NSF, R_SH, R_L, 1000 + s_, pattern_fn) for s_, n in enumerate(counts)]
+    counts_all = synth.batch_cell_counts(64, 2, 10, 0)
+    ws_all = [synth.si_workload(n, NSF, R_SH, R_L, 1000 + s_, pattern_fn) for s_, n in enumerate(counts_all)]
+    world = dist.get_world_size() if dist else 1
+    rank = dist.get_rank() if dist else 0
+    split = None
+    if world > 1:
+        # exact work of each system: the block triples of its evaluation (the
+        # plans' symbolic pass); every rank computes the same assignment
+        work = []
+        for w in ws_all:
+            sy = System(ctx, NSF, "fp32", w["pos"], w["cell"], R_SH, R_L)
+            work.append(sy.triples(True))
+            del sy
+        parts = assign_lpt(work, world)
+        split = {"rule": "whole systems by block-triple count, longest processing time first",
+                 "systems_per_rank": [len(p_) for p_ in parts], "work_per_rank": lpt_loads(work, parts)}
+        ws = [ws_all[i] for i in parts[rank]]
+        counts = [counts_all[i] for i in parts[rank]]
+    else:
+        ws, counts = ws_all, counts_all
+    n_atoms_all = sum(w["pos"].shape[0] for w in ws_all)
     off = [0]
     for w in ws:
         off.append(off[-1] + w["pos"].shape[0])
@@ -498,7 +521,10 @@ def run_batch64(args, ctx):
     S, H, L = (torch.from_numpy(np.concatenate([w[k] for w in ws])).to(ctx.device, dt) for k in ("S", "H", "L"))
     tuned = sysb.autotune(S, H, L, reps=2)
     graph, out, G = sysb.capture(S, H, L)
+    if dist:
+        dist.barrier()
     t_graph = _flush_timed(ctx, graph.replay, args.steps, args.warmup)
+    t_graph = aggregate(t_graph, 1, 1, dist, ctx.device)[1]  # slowest rank
     flops = 2 * NSF ** 3 * sysb.triples(True)
     mirrored = sysb.mirror
     del graph, sysb, S, H, L, out, G
@@ -514,20 +540,22 @@ def run_batch64(args, ctx):
         del sy, Ss, Hs, Ls
         gc.collect()
         torch.cuda.empty_cache()
+    t_sep = aggregate(t_sep, 1, 1, dist, ctx.device)[1]
     line = {
-        "metric": METRIC, "value": round(n_atoms * args.steps / t_graph, 1), "unit": "atoms/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC, "value": round(n_atoms_all * args.steps / t_graph, 1), "unit": "atoms/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t_graph * 1e3 / args.steps, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batch64_si_cells2to10_nsf4_rsh6.6A_rl8A", "systems": 64, "atoms": n_atoms,
-                   "cell_counts": counts, "mode": "one block-diagonal evaluation replayed as a CUDA graph",
-                   "l2": "flushed between timed steps"},
-        "gflops": round(flops * args.steps / t_graph / 1e9, 1),
+        "config": {"workload": "batch64_si_cells2to10_nsf4_rsh6.6A_rl8A", "systems": 64, "atoms": n_atoms_all,
+                   "cell_counts": counts_all, "mode": "one block-diagonal evaluation replayed as a CUDA graph",
+                   "l2": "flushed between timed steps",
+                   "parallelism": split or "one rank"},
+        "gflops_rank0": round(flops * args.steps / t_graph / 1e9, 1),
         "stage_kernels": {k: v[0] for k, v in tuned.items()}, "t_mirrored": mirrored,
-        "per_system_launches": {"value": round(n_atoms * args.steps / t_sep, 1), "unit": "atoms/s",
+        "per_system_launches": {"value": round(n_atoms_all * args.steps / t_sep, 1), "unit": "atoms/s",
                                 "ms_per_step": round(t_sep * 1e3 / args.steps, 4)},
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
         # the FP64 oracle on a bounded sample of the batch: its systems of at
         # most 4^3 cells, in order, each evaluated in full
         import oracle
@@ -718,7 +746,7 @@ def main():
         clocks.start()
         t0 = time.time()
         if args.config == "batch64":
-            line = run_batch64(args, ctx)
+            line = run_batch64(args, ctx, dist)
         elif args.config == "si32768_nsf9":
             line = run_large(args, ctx, 9, 10.0, False)
         elif args.config == "si4096_truncation":
@@ -736,6 +764,9 @@ def main():
             else clocks.summary(t0, time.time())
         if rank == 0:
             print(json.dumps(line), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
         return
     w, _ = build_inputs(ctx, torch.float64)
     # measured FMA-pipe rates (the SIMT products' measured ALU roofline)
