@@ -625,6 +625,8 @@ def run_large(args, ctx, nsf, r_l, autograd):
                    "step": "autograd forward + recompute backward" if autograd else "energy + gradient"},
         "gflops": round(flops * args.steps / t / 1e9, 1),
         "stage_kernels": {k: v[0] for k, v in tuned.items()}, "t_mirrored": sysm.mirror,
+        "stage_tuning_ms": {st: {k: round(v, 3) for k, v in tab.items()} for st, tab in sysm.tune_table.items()},
+        "stage_triples": sysm.stage_triples(),
         "cpu_baseline": {"value": None, "kind": "oracle",
                          "reason": "not run: the FP64 oracle would hold every intermediate of 32768 atoms "
                                    "on the host (T alone is 86 M blocks) and take minutes (NSF=4) to tens "

@@ -190,14 +190,18 @@ lnv_status lnv_plan_product(lnv_ctx *ctx, const lnv_pattern *A, const lnv_patter
  * memory, every operand split into TF32 high and low parts (hi*hi + hi*lo +
  * lo*hi, FP32 accumulation: FP32-level accuracy); needs op(B) = B^T (plans
  * without LNV_TRANS_B fail with LNV_ERR_UNSUPPORTED); FP32 values with NSF =
- * 4 (other cases run kernel 0).
+ * 4 (other cases run kernel 0), 10 the same for 9 x 9 blocks: row groups of
+ * 7 atoms (N = 63 of 64), 128-row tiles of 14 output columns (M = 126 of
+ * 128), K in stages of 8 k-atoms; either op(B); FP32 values with NSF = 9
+ * (other cases run kernel 0); value arrays 16-byte aligned (else
+ * LNV_ERR_UNSUPPORTED from the multiply).
  * The default is 3 when at least half of the table's candidates hit, else 4,
  * when the tables fit a third of the free device memory. */
 lnv_status lnv_plan_info(const lnv_plan *plan, int64_t *triples, int *mode);
 /* Number of product kernels (0 .. LNV_NUM_KERNELS - 1). */
-#define LNV_NUM_KERNELS 10
-/* Select the kernel of a plan (0..9 as above); all give the same result up
- * to rounding order.  Kernels 3-9 build their tables on first selection
+#define LNV_NUM_KERNELS 11
+/* Select the kernel of a plan (0..10 as above); all give the same result up
+ * to rounding order.  Kernels 3-10 build their tables on first selection
  * (allocates, synchronises).  LNV_ERR_UNSUPPORTED if the kernel cannot run
  * this plan. */
 lnv_status lnv_plan_set_kernel(lnv_ctx *ctx, lnv_plan *plan, int kernel);

@@ -284,12 +284,13 @@ static lnv_status group_plan_lists(lnv_ctx *ctx, lnv_plan *pl, int G, size_t bud
     if (s == LNV_OK) s = upload(b_off, &gp.bidx_off, &bytes);
     if (s == LNV_OK && jmajor) {
         // CTA work items of the tensor-core kernel: (group, first column) per
-        // kTcCols columns of J, ordered by that first column's atom, then by
+        // kTcCols (kTc9Cols) columns of J, ordered by that first column's atom, then by
         // group, so that the CTAs running at one time cover nearby columns
         // (and share the rows of op(B) they gather) across many groups
+        const int cols = G == kTc9G ? kTc9Cols : kTcCols;
         std::vector<std::pair<std::pair<uint64_t, int64_t>, int2>> it;
         for (int64_t g = 0; g < ng; ++g)
-            for (int64_t c0 = 0; c0 < nj[g]; c0 += kTcCols)
+            for (int64_t c0 = 0; c0 < nj[g]; c0 += cols)
                 it.push_back({{(uint64_t)j_list[j_off[g] + c0], g}, make_int2((int)g, (int)c0)});
         std::sort(it.begin(), it.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
         std::vector<int2> items(it.size());

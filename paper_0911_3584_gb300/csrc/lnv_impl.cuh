@@ -117,7 +117,8 @@ struct GroupPlan {
     // the tensor-core kernel's form: J in atom order (spatial order for
     // cell-ordered atoms), bidx j-major (bidx[j][k], rows of nk_pad(g) entries, a
     // multiple of 4) and the CTA work items (group, first column of J) of
-    // kTcCols columns each, sorted by the key of the item's first column
+    // kTcCols (kTc9Cols for 7-row groups) columns each, sorted by the key of
+    // the item's first column
     int jmajor = 0;
     int apos_op = 0;             // apos holds op(A)'s stored block (transposed through tr)
     int2 *items = nullptr;       // [n_items]
@@ -127,6 +128,10 @@ struct GroupPlan {
 
 // Columns j per CTA of the tensor-core kernel (two 128-row tiles of 32 atoms).
 constexpr int kTcCols = 64;
+// Its NSF = 9 form (kernel 10): groups of 7 rows (N = 63 of 64), one tile of
+// 14 columns (M = 126 of 128) per CTA.
+constexpr int kTc9G = 7;
+constexpr int kTc9Cols = 14;
 
 // Triple-list plan of a product (see triples.cu): C's blocks as work items,
 // ordered by groups of 4 rows, then column, then row inside the group; for
@@ -213,8 +218,11 @@ lnv_status group_plan_build_into(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budge
 // Kernel 9 (umma.cu): C = mask(op(A) B^T) on 8-row groups, tcgen05 tensor
 // cores, FP32 values, NSF = 4.
 lnv_status launch_umma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B, void *C);
-// Finish kernel 9's tables after they are built (op(A) positions for A^T).
+// Finish kernel 9's or 10's tables after they are built (op(A) positions for A^T).
 lnv_status umma_prepare(lnv_ctx *ctx, lnv_plan *pl);
+// Kernel 10 (umma9.cu): C = mask(op(A) op(B)) on 7-row groups, tcgen05 tensor
+// cores, FP32 values, NSF = 9.
+lnv_status launch_umma9(lnv_ctx *ctx, const lnv_plan *pl, bool ta, bool tb, const void *A, const void *B, void *C);
 lnv_status scan_exclusive(cudaStream_t st, const int64_t *in, int64_t n, int64_t *out);
 void group_plan_free(GroupPlan *gp);
 // Triple-list plan (triples.cu); LNV_ERR_UNSUPPORTED when it would not fit the budget.

@@ -19,6 +19,8 @@
 //  7  listed triples: per output block its (A, B) pairs, listed once per plan.
 //  9  row groups of 8 rows as dense tiles on the tcgen05 tensor cores (umma.cu):
 //     FP32 values, NSF = 4, op(B) = B^T, split-TF32 operands.
+//  10 the same for NSF = 9 (umma9.cu): row groups of 7 rows, tiles of 14
+//     output columns, either op(B).
 //
 // A product declared symmetric (LNV_SYM_C, T = SLS) may be formed on its
 // upper triangle and mirrored (mirror_lower).  Sums are formed in k order in
@@ -272,7 +274,7 @@ lnv_status plan_pull_items(lnv_plan *pl)
 
 lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
 {
-    LNV_ARG(pl && kernel >= 0 && kernel < LNV_NUM_KERNELS, "kernel must be 0..9");
+    LNV_ARG(pl && kernel >= 0 && kernel < LNV_NUM_KERNELS, "kernel must be 0..10");
     if (kernel == 2) {
         if (!pl->B->symmetric) {
             set_error("the merge-join pull needs a symmetric B pattern");
@@ -290,6 +292,12 @@ lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
         LNV_TRY(group_plan_build_into(ctx, pl, 8, free_b / 3, true, false, pl->tc));
+        LNV_TRY(umma_prepare(ctx, pl));
+    } else if (kernel == 10) {
+        // 7-row group tables with the dense position table (either op(B))
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        LNV_TRY(group_plan_build_into(ctx, pl, kTc9G, free_b / 3, true, false, pl->tc));
         LNV_TRY(umma_prepare(ctx, pl));
     } else if (kernel == 7) {
         size_t free_b = 0, total_b = 0;
@@ -323,7 +331,7 @@ lnv_status plan_set_split(lnv_ctx *ctx, lnv_plan *pl, int on)
 void plan_trim(lnv_plan *plan)
 {
     if (plan->mode != 7) triple_plan_free(&plan->tri);
-    if (plan->mode != 9) group_plan_free(&plan->tc);
+    if (plan->mode != 9 && plan->mode != 10) group_plan_free(&plan->tc);
     GroupPlan &gp = plan->grp;
     const bool dense = plan->mode == 3 || plan->mode == 5 || plan->mode == 6 || plan->mode == 8,
                sparse = plan->mode == 4;

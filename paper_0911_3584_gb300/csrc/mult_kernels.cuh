@@ -1633,6 +1633,18 @@ lnv_status dispatch_mode(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const 
             return launch_push2<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, pl->sym1 && pl->split);
         }
     }
+    if (pl->mode == 10) {
+        // tcgen05 tensor cores for 9 x 9 blocks: FP32 values, NSF = 9, either
+        // transpose; other cases run the push kernel, which needs no tables
+        if constexpr (NSF == 9 && sizeof(T) == 4) {
+            LNV_TRY(launch_umma9(ctx, pl, TA, TB, A, B1, C1));
+            if (B2) LNV_TRY(launch_umma9(ctx, pl, TA, TB, A, B2, C2));
+            return LNV_OK;
+        } else {
+            if (B2) return launch_push2<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, pl->sym1 && pl->split);
+            return launch_push2<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, pl->sym1 && pl->split);
+        }
+    }
     if (pl->mode == 7) {
         if constexpr (NSF == 4) {
             // two fused FP32 products; FP64 runs them one at a time (registers)

@@ -15,7 +15,8 @@
 //    along K, the stride byte offset (SBO) between groups of 8 rows.
 //  - FP32 operands are read as TF32: the tensor core ignores the low 13
 //    bits of the significand (truncation; checked on GB300 against a CPU
-//    reference of truncated operands).
+//    reference of truncated operands).  The split below hands it values
+//    already rounded to TF32, so nothing is truncated.
 //
 // Every wait below is bounded by a time limit: a wait that runs out raises a
 // flag in shared memory that every other wait of the CTA observes, so the
@@ -158,25 +159,35 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 }
 
 // ---- operand split for 3xTF32 --------------------------------------------------
-// x = hi + lo with hi exactly representable in TF32 (x with the low 13
-// significand bits cleared) and lo = x - hi exact in FP32; the tensor core
-// then reads lo as TF32 (relative error 2^-10 of lo, about 2^-20 of x).
+// x = hi + lo + r with hi = x rounded to the nearest TF32 value, lo = x - hi
+// (exact in FP32) rounded to the nearest TF32 value, |r| <= 2^-22 |x|.  Both
+// roundings are to nearest: truncation (what the tensor core applies to FP32
+// operands) leaves lo, and the dropped lo*lo term, with the sign of x, an
+// error that adds up over long sums instead of cancelling.
+__device__ __forceinline__ float tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
 {
-    hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-    lo = x - hi;
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - hi);
 }
 // The same for two values at once (one packed FP32 subtraction; x - hi is
-// exact, so the rounding mode does not matter).
+// exact, so its rounding mode does not matter).
 __device__ __forceinline__ void split_tf32x2(float x0, float x1, float &h0, float &h1, float &l0, float &l1)
 {
-    h0 = __uint_as_float(__float_as_uint(x0) & 0xFFFFE000u);
-    h1 = __uint_as_float(__float_as_uint(x1) & 0xFFFFE000u);
+    h0 = tf32_rna(x0);
+    h1 = tf32_rna(x1);
     unsigned long long x, h, l;
     asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(x0), "f"(x1));
     asm("mov.b64 %0, {%1, %2};" : "=l"(h) : "f"(h0), "f"(h1));
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(l) : "l"(x), "l"(h));
     asm("mov.b64 {%0, %1}, %2;" : "=f"(l0), "=f"(l1) : "l"(l));
+    l0 = tf32_rna(l0);
+    l1 = tf32_rna(l1);
 }
 
 

@@ -406,7 +406,7 @@ lnv_status umma_prepare(lnv_ctx *ctx, lnv_plan *pl)
     if (pl->trans_a && !gp.apos_op && gp.apos && gp.n_groups > 0) {
         int64_t n = 0;
         LNV_CUDA(cudaMemcpy(&n, gp.k_off + gp.n_groups, sizeof(int64_t), cudaMemcpyDeviceToHost));
-        n *= kTcG;
+        n *= gp.G;
         if (n > 0) {
             k_apos_transpose<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1 << 20), 256, 0, ctx->stream>>>(
                 n, gp.apos, pl->A->tr);

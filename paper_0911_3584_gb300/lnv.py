@@ -299,7 +299,7 @@ class Plan:
         self.triples, self.mode = t.value, self.KERNELS[m.value]
 
     KERNELS = ("push", "pull", "pull-merge", "group", "group-sparse", "group-pipe", "group-mma", "triples",
-               "group-pipe-half", "tensor")
+               "group-pipe-half", "tensor", "tensor9")
 
     def set_kernel(self, kernel):
         k = self.KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)

@@ -123,7 +123,8 @@ def _set_kernel_or_refused(plan, kernel, tb):
 
 
 @pytest.mark.parametrize("kernel", ["default", "push", "pull", "pull-merge", "group", "group-sparse",
-                                    "group-pipe", "group-mma", "triples", "group-pipe-half", "tensor"])
+                                    "group-pipe", "group-mma", "triples", "group-pipe-half", "tensor",
+                                    "tensor9"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("nsf", [1, 2, 4, 9])
 @pytest.mark.parametrize("case", PRODUCT_CASES)
@@ -148,7 +149,7 @@ def test_masked_product_matches_oracle(ctx, dtype, nsf, case, kernel):
 
 
 @pytest.mark.parametrize("kernel", ["default", "push", "pull", "pull-merge", "group", "group-sparse",
-                                    "group-pipe", "group-mma", "triples", "group-pipe-half"])
+                                    "group-pipe", "group-mma", "triples", "group-pipe-half", "tensor9"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("nsf", [1, 4, 9])
 def test_symmetric_product_formed_on_one_triangle(ctx, dtype, nsf, kernel):
@@ -278,6 +279,49 @@ def test_transposed_product_ragged_groups(ctx, kernel, n_atoms):
         C = plan.multiply(to_dev(A["val"], torch.float32, ctx.device), to_dev(B["val"], torch.float32, ctx.device))
         ref = oracle.mprod(oracle.transpose(A) if ta else A, oracle.transpose(B), oc)
         assert rel_fro(C.cpu().numpy(), ref["val"]) <= TOL[torch.float32][0], (ta, plan.mode)
+
+
+@pytest.mark.parametrize("n_atoms", [1, 6, 7, 8, 15, 29, 61])
+def test_tensor9_product_ragged_groups(ctx, n_atoms):
+    """Kernel 10 (NSF = 9) on atom counts that leave a partial last 7-row group
+    and partial 14-column tiles, random clustered positions, every operand
+    transpose: FP32 against the oracle."""
+    rng = np.random.default_rng(100 + n_atoms)
+    cell = np.array([20.0, 20.0, 20.0])
+    pos = rng.uniform(0, 9.0, size=(n_atoms, 3))
+    ra, rb, rc = 4.0, 7.0, 6.0
+    PA, PB, PC = (Pattern.build(ctx, pos, cell, r) for r in (ra, rb, rc))
+    oa, ob, oc = (oracle.pattern(pos, cell, r) for r in (ra, rb, rc))
+    A = rounded(oracle.csr(*oa, rng.standard_normal((oa[1].size, 9, 9))), torch.float32)
+    B = rounded(oracle.csr(*ob, rng.standard_normal((ob[1].size, 9, 9))), torch.float32)
+    for ta in (False, True):
+        for tb in (False, True):
+            plan = Plan(ctx, PA, PB, PC, trans_a=ta, trans_b=tb)
+            plan.set_kernel("tensor9")
+            C = plan.multiply(to_dev(A["val"], torch.float32, ctx.device),
+                              to_dev(B["val"], torch.float32, ctx.device))
+            ref = oracle.mprod(oracle.transpose(A) if ta else A, oracle.transpose(B) if tb else B, oc)
+            assert rel_fro(C.cpu().numpy(), ref["val"]) <= TOL[torch.float32][0], (ta, tb)
+    assert ctx.device_status() == 0
+
+
+def test_tensor9_repeated_calls_are_identical(ctx):
+    """Kernel 10 sums in a fixed order: two launches give bit-identical output."""
+    w, S, H, L = workload(2, 9, 6.6, 8.0, seed=6)
+    pos, cell = w["pos"], w["cell"]
+    PL, PT, PX = (Pattern.build(ctx, pos, cell, r) for r in (8.0, 21.2, 14.6))
+    ot = oracle.pattern(pos, cell, 21.2)
+    T = oracle.csr(*ot, np.random.default_rng(3).standard_normal((ot[1].size, 9, 9)))
+    plan = Plan(ctx, PL, PT, PX, trans_b=True)
+    plan.set_kernel("tensor9")
+    Ld, Td = to_dev(L["val"], torch.float32, ctx.device), to_dev(T["val"], torch.float32, ctx.device)
+    c1 = plan.multiply(Ld, Td).cpu().numpy()
+    c2 = plan.multiply(Ld, Td).cpu().numpy()
+    assert np.array_equal(c1, c2)
+    ref = oracle.mprod(rounded(L, torch.float32), oracle.transpose(rounded(T, torch.float32)),
+                       oracle.pattern(pos, cell, 14.6))
+    assert rel_fro(c1, ref["val"]) <= TOL[torch.float32][0]
+    assert ctx.device_status() == 0
 
 
 def test_tensor_kernel_repeated_calls_are_identical(ctx):
@@ -462,6 +506,25 @@ def test_lnv_512_atoms_tensor_core_products(ctx, si512, stages):
     assert ctx.device_status() == 0
 
 
+@pytest.mark.parametrize("ncell", [2, 3])
+def test_lnv_nsf9_tensor_core_products(ctx, ncell):
+    """NSF = 9 systems (s, p, d) with every product stage on the tcgen05 kernel
+    (10), every output against the FP64 oracle at the FP32 bound."""
+    w, S, H, L = workload(ncell, 9, 6.6, 8.0, seed=17 + ncell)
+    sysm = System(ctx, 9, "fp32", w["pos"], w["cell"], 6.6, 8.0)
+    for st in ("XY", "TU", "Z", "Q", "W"):
+        sysm.set_stage_kernel(st, "tensor9")
+    assert all(k == "tensor9" for k in sysm.stage_kernels().values())
+    dev = ctx.device
+    Sd, Hd, Ld = (to_dev(M["val"], torch.float32, dev) for M in (S, H, L))
+    ref = oracle_lnv(w, rounded(S, torch.float32), rounded(H, torch.float32), rounded(L, torch.float32))
+    for mirror in (True, False):
+        sysm.set_mirror(mirror)
+        out, G = sysm.energy_grad(Sd, Hd, Ld)
+        _check_lnv(out.cpu().numpy(), G.cpu().numpy(), ref, torch.float32)
+    assert ctx.device_status() == 0
+
+
 def test_lnv_4096_atoms_tensor_core_products(ctx, si4096):
     """The benchmark workload with Z and W on the tcgen05 kernel."""
     w, ref = si4096
@@ -506,6 +569,7 @@ def test_32768_atoms_sampled_rows_bench_configuration(ctx, nsf):
     S, H, L = (oracle.csr(w[rp], w[c], w[k].astype(np.float32).astype(np.float64))
                for rp, c, k in (("sh_row_ptr", "sh_col", "S"), ("sh_row_ptr", "sh_col", "H"),
                                 ("l_row_ptr", "l_col", "L")))
+    assert ctx.device_status() == 0
     ref = lnv_grad_rows(S, H, L, [7, 16411, 32767])
     g = G.double().cpu().numpy()[ref["pos"]]
     gn = GN.double().cpu().numpy()[ref["pos"]]
