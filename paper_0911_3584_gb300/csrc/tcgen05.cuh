@@ -103,6 +103,27 @@ __device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, uin
         if (global_ns() - t0 > limit_ns) return false;
     }
 }
+// Add `bytes` to the transfer count the barrier's current phase waits for.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bulk copy global -> shared memory of this CTA (the TMA engine, no tensor
+// map): both addresses 16-byte aligned, bytes a multiple of 16; its bytes
+// count toward the barrier's transfer count.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst_smem),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// Arrive on the barrier once every cp.async this thread issued so far has
+// landed (the arrival is not counted in advance: the barrier's count includes it).
+__device__ __forceinline__ void cp_async_mbar_arrive(uint32_t bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
 // Arrive on the barrier once every tcgen05 operation this thread issued so far
 // has completed.
 __device__ __forceinline__ void commit(uint32_t bar)
