@@ -142,6 +142,10 @@ struct TriplePlan {
     int32_t *item_cb = nullptr;  // [n_items]     C block of the item
     int64_t *t_off = nullptr;    // [n_items + 1] item's range in tri
     int2 *tri = nullptr;         // [triples]     (A block, B block) storage positions
+    // plans with a symmetric first output: the items of C's blocks with
+    // col >= row, in item order (the first output formed on its upper triangle)
+    int32_t *up = nullptr;       // [n_up] item indices
+    int64_t n_up = 0;
     size_t bytes = 0;
 };
 

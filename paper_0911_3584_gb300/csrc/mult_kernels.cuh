@@ -1,6 +1,7 @@
 // Kernels of the masked block products; instantiated per (precision, NSF) in
 // mult_inst_*.cu so that the library compiles in parallel.
 #pragma once
+#include <type_traits>
 #include <algorithm>
 
 #include "lnv_impl.cuh"
@@ -1125,17 +1126,19 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
 // product; the next pair's blocks are fetched while the current ones are
 // applied.  Nothing is multiplied that is absent or discarded.  Items are
 // ordered by groups of four rows, then column, so the warps that run together
-// share most blocks and hit in L1.
+// share most blocks and hit in L1.  With sub (not null) the launch covers the
+// items sub[0 .. n_items - 1] only (the upper triangle of a symmetric output).
 template <typename T, int NOUT, bool TA, bool TB>
 __global__ void __launch_bounds__(128)
-k_tri(int64_t n_items, const int32_t *__restrict__ item_cb, const int64_t *__restrict__ t_off,
-      const int2 *__restrict__ tri, const T *__restrict__ a_val, const T *__restrict__ b_val1,
-      const T *__restrict__ b_val2, T *__restrict__ c_val1, T *__restrict__ c_val2)
+k_tri(int64_t n_items, const int32_t *__restrict__ sub, const int32_t *__restrict__ item_cb,
+      const int64_t *__restrict__ t_off, const int2 *__restrict__ tri, const T *__restrict__ a_val,
+      const T *__restrict__ b_val1, const T *__restrict__ b_val2, T *__restrict__ c_val1, T *__restrict__ c_val2)
 {
     constexpr int BS = 16;
-    const int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2;
+    const int64_t iq = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2;
     const int x = threadIdx.x & 3;
-    if (it >= n_items) return;
+    if (iq >= n_items) return;
+    const int64_t it = sub ? (int64_t)sub[iq] : iq;
     const int64_t t0 = t_off[it], t1 = t_off[it + 1];
     T acc[NOUT][4];
 #pragma unroll
@@ -1489,9 +1492,11 @@ lnv_status launch_gmma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const vo
     return LNV_OK;
 }
 
+// upper1: the first output is formed on its upper triangle only (a plan with
+// a symmetric first output and the split on; the caller mirrors the rest).
 template <typename T, int NOUT, bool TA, bool TB>
 lnv_status launch_tri(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1, const void *B2,
-                      void *C1, void *C2)
+                      void *C1, void *C2, bool upper1)
 {
     const TriplePlan &tp = pl->tri;
     if (tp.n_items == 0) return LNV_OK;
@@ -1499,9 +1504,24 @@ lnv_status launch_tri(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const voi
         set_error("plan lacks its triple lists");
         return LNV_ERR_UNSUPPORTED;
     }
-    const int64_t threads = tp.n_items * 4;
-    k_tri<T, NOUT, TA, TB><<<(unsigned)((threads + 127) / 128), 128, 0, ctx->stream>>>(
-        tp.n_items, tp.item_cb, tp.t_off, tp.tri, (const T *)A, (const T *)B1, (const T *)B2, (T *)C1, (T *)C2);
+    auto run = [&](const int32_t *sub, int64_t n, const void *b1, const void *b2, void *c1, void *c2, auto nout) {
+        constexpr int NO = decltype(nout)::value;
+        if (n == 0) return;
+        k_tri<T, NO, TA, TB><<<(unsigned)((n * 4 + 127) / 128), 128, 0, ctx->stream>>>(
+            n, sub, tp.item_cb, tp.t_off, tp.tri, (const T *)A, (const T *)b1, (const T *)b2, (T *)c1, (T *)c2);
+    };
+    if (upper1 && tp.up) {
+        // the symmetric first output on its upper triangle, the second one
+        // everywhere
+        run(tp.up, tp.n_up, B1, nullptr, C1, nullptr, std::integral_constant<int, 1>{});
+        LNV_LAUNCHED();
+        if (NOUT == 2) {
+            run(nullptr, tp.n_items, B2, nullptr, C2, nullptr, std::integral_constant<int, 1>{});
+            LNV_LAUNCHED();
+        }
+        return LNV_OK;
+    }
+    run(nullptr, tp.n_items, B1, B2, C1, C2, std::integral_constant<int, NOUT>{});
     LNV_LAUNCHED();
     return LNV_OK;
 }
@@ -1648,9 +1668,10 @@ lnv_status dispatch_mode(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const 
     if (pl->mode == 7) {
         if constexpr (NSF == 4) {
             // two fused FP32 products; FP64 runs them one at a time (registers)
-            if (B2 && sizeof(T) == 4) return launch_tri<T, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2);
-            LNV_TRY((launch_tri<T, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr)));
-            if (B2) LNV_TRY((launch_tri<T, 1, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr)));
+            const bool up = pl->sym1 && pl->split;
+            if (B2 && sizeof(T) == 4) return launch_tri<T, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, up);
+            LNV_TRY((launch_tri<T, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, up)));
+            if (B2) LNV_TRY((launch_tri<T, 1, TA, TB>(ctx, pl, A, B2, nullptr, C2, nullptr, false)));
             return LNV_OK;
         } else {
             // other block sizes: the push kernel, which needs no tables

@@ -210,6 +210,20 @@ __device__ __forceinline__ void split_tf32x2(float x0, float x1, float &h0, floa
     l0 = tf32_rna(l0);
     l1 = tf32_rna(l1);
 }
+// The cheaper split of kernels whose producer threads are bound by their
+// instruction count: hi = x with the low 13 significand bits cleared, lo = x
+// - hi exact in FP32 (the tensor core then truncates lo to TF32: lo and the
+// dropped lo*lo term carry the sign of x, a bias of about 2^-21 relative).
+__device__ __forceinline__ void split_tf32x2_trunc(float x0, float x1, float &h0, float &h1, float &l0, float &l1)
+{
+    h0 = __uint_as_float(__float_as_uint(x0) & 0xFFFFE000u);
+    h1 = __uint_as_float(__float_as_uint(x1) & 0xFFFFE000u);
+    unsigned long long x, h, l;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(x0), "f"(x1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(h) : "f"(h0), "f"(h1));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(l) : "l"(x), "l"(h));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l0), "=f"(l1) : "l"(l));
+}
 
 
 // 16-byte asynchronous copy global -> shared (zero-filled when src_bytes = 0),

@@ -64,6 +64,7 @@ void triple_plan_free(TriplePlan *tp)
     cudaFree(tp->item_cb);
     cudaFree(tp->t_off);
     cudaFree(tp->tri);
+    cudaFree(tp->up);
     *tp = TriplePlan();
 }
 
@@ -162,6 +163,25 @@ lnv_status triple_plan_build(lnv_ctx *ctx, lnv_plan *pl, size_t budget_bytes)
         }
     }
     cudaFree(cnt);
+    if (s == LNV_OK && pl->sym1) {
+        // the items of C's upper triangle (col >= row), in item order
+        std::vector<int32_t> row_of((size_t)C->nnzb);
+        for (int64_t r = 0; r < n; ++r)
+            for (int64_t q = C->h_row_ptr[r]; q < C->h_row_ptr[r + 1]; ++q) row_of[(size_t)q] = (int32_t)r;
+        std::vector<int32_t> up;
+        up.reserve(items.size() / 2 + 1);
+        for (size_t t = 0; t < items.size(); ++t)
+            if (C->h_col[(size_t)items[t]] >= row_of[(size_t)items[t]]) up.push_back((int32_t)t);
+        tp.n_up = (int64_t)up.size();
+        if (!up.empty()) {
+            if (cudaMalloc(&tp.up, sizeof(int32_t) * up.size()) != cudaSuccess ||
+                cudaMemcpy(tp.up, up.data(), sizeof(int32_t) * up.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+                set_error("triple-list plan: allocation of the upper-triangle items failed");
+                s = LNV_ERR_OOM;
+            }
+            bytes += sizeof(int32_t) * up.size();
+        }
+    }
     if (s != LNV_OK) {
         if (s == LNV_ERR_CUDA) set_error("triple-list plan: kernel failed");
         triple_plan_free(&tp);
