@@ -36,7 +36,7 @@ STAGE_KERNEL = {"XY": "X=LS, Y=LH", "TU": "T=SX, U=SY", "Z": "Z=L T^T", "Q": "Q=
 KERNEL_NAME = {"push": "k_push2", "pull": "k_pull", "pull-merge": "k_pull2", "group": "k_grp",
                "group-sparse": "k_grp (hit lists)", "group-pipe": "k_gw", "group-mma": "k_gmma",
                "triples": "k_tri", "group-pipe-half": "k_gw (half-width slices)",
-               "tensor": "k_umma (tcgen05, 3xTF32)"}
+               "tensor": "k_umma (tcgen05, 3xTF32)", "tensor9": "k_umma9 (tcgen05, 3xTF32, NSF = 9)"}
 
 
 def parse():
@@ -140,7 +140,7 @@ class Clocks:
 
 def product_source_sha():
     h = hashlib.sha1()
-    for f in ("mult_kernels.cuh", "mult.cu", "umma.cu", "tcgen05.cuh", "group.cu"):
+    for f in ("mult_kernels.cuh", "mult.cu", "umma.cu", "umma9.cu", "tcgen05.cuh", "group.cu", "triples.cu"):
         with open(os.path.join(ROOT, "paper_0911_3584_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -616,6 +616,19 @@ def run_large(args, ctx, nsf, r_l, autograd):
     t = _flush_timed(ctx, step, args.steps, args.warmup)
     peak = torch.cuda.max_memory_allocated(ctx.device)
     flops = 2 * nsf ** 3 * (sysm.triples(True) + (sysm.triples(False) if autograd else 0))
+    # stages on the tcgen05 kernels: one-pass algorithmic flops per tuned stage
+    # time against the dense TF32 peak (half the measured BF16 burst)
+    pk = measured_peaks()
+    st_tr = sysm.stage_triples()
+    tensor_stages = []
+    for st, (k, ms) in tuned.items():
+        if k in ("tensor", "tensor9") and ms > 0:
+            ach = 2 * nsf ** 3 * st_tr[st] / (ms * 1e-3) / 1e12
+            tensor_stages.append({"stage": st, "kernel": KERNEL_NAME.get(k, k), "bound": "tensor",
+                                  "achieved": round(ach, 3), "peak": round(pk["bf16_tflops"] / 2, 1),
+                                  "unit": "TFLOP/s", "frac": round(ach / (pk["bf16_tflops"] / 2), 4),
+                                  "kernel_ms": round(ms, 3),
+                                  "peak_source": f"dense TF32 = measured BF16 burst / 2 ({pk['source']})"})
     line = {
         "metric": METRIC, "value": round(n_atoms * args.steps / t, 1), "unit": "atoms/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 3),
@@ -626,7 +639,8 @@ def run_large(args, ctx, nsf, r_l, autograd):
         "gflops": round(flops * args.steps / t / 1e9, 1),
         "stage_kernels": {k: v[0] for k, v in tuned.items()}, "t_mirrored": sysm.mirror,
         "stage_tuning_ms": {st: {k: round(v, 3) for k, v in tab.items()} for st, tab in sysm.tune_table.items()},
-        "stage_triples": sysm.stage_triples(),
+        "stage_triples": st_tr,
+        "roofline_tensor_stages": tensor_stages,
         "cpu_baseline": {"value": None, "kind": "oracle",
                          "reason": "not run: the FP64 oracle would hold every intermediate of 32768 atoms "
                                    "on the host (T alone is 86 M blocks) and take minutes (NSF=4) to tens "

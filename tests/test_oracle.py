@@ -508,3 +508,56 @@ def test_truncated_oracle_against_dense_masked_definition(nsf, r_x, r_t):
     W_bad = blk.T * W + (strict.T * W).T
     G_bad = from_dense(Ml * (6 * (U + U.T) - 4 * (Q.T + W_bad + Q)), L["rp"], L["col"], nsf)
     assert np.linalg.norm(G_bad - G) > 1e-6 * np.linalg.norm(G)
+
+
+# ---------------------------------------------------------------- precision reading
+
+def _tf32(x):
+    """x rounded to the nearest TF32 value (10 explicit significand bits, ties
+    away from zero), held in FP32."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    return ((u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def _lnv_emulated(S, H, L, mm):
+    """Eq. 3's E, N_e and dE/dL with every matrix product formed by mm (FP32
+    intermediates) and the traces and combinations in FP64."""
+    f = lambda M: np.asarray(M, dtype=np.float32)
+    S, H, L = f(S), f(H), f(L)
+    LS, LH = mm(L, S), mm(L, H)
+    SLS, SLH = mm(S, LS), mm(S, LH)
+    LSLS = mm(L, SLS)
+    K = 3.0 * mm(LS, L).astype(np.float64) - 2.0 * mm(LSLS, L).astype(np.float64)
+    E = 2.0 * np.sum(K * H.T.astype(np.float64))
+    Ne = 2.0 * np.sum(K * S.T.astype(np.float64))
+    HLS, HLSLS, SLSLH, SLHLS = mm(H, LS), mm(H, LSLS), mm(SLS, LH), mm(SLH, LS)
+    G = 6.0 * (SLH.astype(np.float64) + HLS) - 4.0 * (SLSLH.astype(np.float64) + SLHLS + HLSLS)
+    return E, Ne, G
+
+
+def test_single_pass_tf32_misses_the_fp32_bound():
+    """The reading behind the tensor-core kernels' split operands: with every
+    product's operands rounded once to TF32 (FP32 accumulation, emulated on the
+    CPU) the gradient of a 64-atom NSF = 4 system misses the FP32 path's bound
+    of 2e-5 relative, while the hi*hi + hi*lo + lo*hi split (3xTF32) meets it."""
+    w = synth.si_workload(2, 4, 6.6, 8.0, 5, oracle.pattern)
+    S = to_dense(w["sh_row_ptr"], w["sh_col"], w["S"])
+    H = to_dense(w["sh_row_ptr"], w["sh_col"], w["H"])
+    L = to_dense(w["l_row_ptr"], w["l_col"], w["L"])
+    S32, H32, L32 = (M.astype(np.float32).astype(np.float64) for M in (S, H, L))
+    E0, N0, G0, _ = lnv_dense(S32, H32, L32)
+
+    def one_pass(A, B):
+        return _tf32(A) @ _tf32(B)
+
+    def three_pass(A, B):
+        Ah, Bh = _tf32(A), _tf32(B)
+        Al, Bl = _tf32(A - Ah), _tf32(B - Bh)
+        return (Ah @ Bh + Ah @ Bl) + Al @ Bh
+
+    errs = {}
+    for name, mm in (("1xTF32", one_pass), ("3xTF32", three_pass)):
+        E, Ne, G = _lnv_emulated(S32, H32, L32, mm)
+        errs[name] = (abs(E - E0) / abs(E0), abs(Ne - N0) / abs(N0), np.linalg.norm(G - G0) / np.linalg.norm(G0))
+    assert errs["1xTF32"][2] > 2e-5, errs
+    assert max(errs["3xTF32"]) < 2e-5, errs
