@@ -527,16 +527,26 @@ def run_batch64(args, ctx, dist=None):
     t_graph = aggregate(t_graph, 1, 1, dist, ctx.device)[1]  # slowest rank
     flops = 2 * NSF ** 3 * sysb.triples(True)
     mirrored = sysb.mirror
+    # where the union gains or loses: its stage times (one profiled, uncaptured
+    # evaluation) against the per-system stage times summed below
+    sysb.profile(True)
+    sysb.energy_grad(S, H, L)
+    stage_union = sysb.stage_ms()
     del graph, sysb, S, H, L, out, G
     gc.collect()
     torch.cuda.empty_cache()
     # per-system launches: each system on its own, autotuned the same way
     t_sep = 0.0
+    stage_sep = {}
     for w in ws:
         sy = System(ctx, NSF, "fp32", w["pos"], w["cell"], R_SH, R_L)
         Ss, Hs, Ls = (torch.from_numpy(w[k]).to(ctx.device, dt) for k in ("S", "H", "L"))
         sy.autotune(Ss, Hs, Ls, reps=1)
         t_sep += _flush_timed(ctx, lambda: sy.energy_grad(Ss, Hs, Ls), args.steps, args.warmup)
+        sy.profile(True)
+        sy.energy_grad(Ss, Hs, Ls)
+        for k_, v_ in sy.stage_ms().items():
+            stage_sep[k_] = stage_sep.get(k_, 0.0) + v_
         del sy, Ss, Hs, Ls
         gc.collect()
         torch.cuda.empty_cache()
@@ -554,6 +564,8 @@ def run_batch64(args, ctx, dist=None):
         "stage_kernels": {k: v[0] for k, v in tuned.items()}, "t_mirrored": mirrored,
         "per_system_launches": {"value": round(n_atoms_all * args.steps / t_sep, 1), "unit": "atoms/s",
                                 "ms_per_step": round(t_sep * 1e3 / args.steps, 4)},
+        "stage_ms_union_vs_per_system_sum": {k_: [round(stage_union.get(k_, 0.0), 3), round(v_, 3)]
+                                             for k_, v_ in stage_sep.items()},
     }
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         # the FP64 oracle on a bounded sample of the batch: its systems of at
