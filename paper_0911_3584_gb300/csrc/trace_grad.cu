@@ -6,8 +6,8 @@
 // in FP64 (lanes over blocks, then a fixed butterfly), rows are reduced per
 // system by one CTA in a fixed order: the result is run-to-run deterministic.
 // The generic kernel widens FP32 operands to FP64 before multiplying
-// (exactly); the fused four-trace kernel forms each block's 16-term dot
-// product in the value precision and sums the blocks in FP64.
+// (exactly); the fused four-trace kernels (NSF = 4 and 9) form each block's
+// dot products in the value precision and sum the blocks in FP64.
 //
 // Gradient: dE/dL = 6(SLH + HLS) - 4(SLSLH + SLHLS + HLSLS) on L's range.
 // With U = SLH (on the R_T pattern), W = SLHLS (symmetric, kept on the upper
@@ -114,6 +114,84 @@ k_trace_lnv4(int64_t n, const int64_t *__restrict__ rp, const int64_t *__restric
                 a2 = fma(c, by, a2);
                 a3 = fma(a, bx, a3);
                 a4 = fma(c, bx, a4);
+            }
+        t1 += (double)a1;
+        t2 += (double)a2;
+        n1 += (double)a3;
+        n2 += (double)a4;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+        t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+        n1 += __shfl_xor_sync(0xffffffffu, n1, o);
+        n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    }
+    if (lane == 0) {
+        row_part[i] = t1;
+        row_part[n + i] = t2;
+        row_part[2 * n + i] = n1;
+        row_part[3 * n + i] = n2;
+    }
+}
+
+// The same four traces with 9 x 9 blocks.  One warp per row takes the row's
+// blocks one after another, the 81 elements of a block over its lanes
+// (lane e holds e, e + 32, e + 64): X_p and Z_p are read in order, the
+// partner blocks X_q and Y_q (q = tr p) at the transposed index 9 z + x,
+// so every load of the warp covers one block.  Four blocks are loaded
+// before any is used; each lane's share of their four dot products (12
+// products per trace) is formed in the value precision and added to FP64
+// sums; a fixed butterfly ends the row.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_trace_lnv9(int64_t n, const int64_t *__restrict__ rp, const int64_t *__restrict__ tr,
+             const T *__restrict__ X, const T *__restrict__ Y, const T *__restrict__ Z,
+             double *__restrict__ row_part)
+{
+    constexpr int BS = 81, U = 4;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    int e[3], et[3];
+    bool ev[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        e[c] = lane + 32 * c;
+        ev[c] = e[c] < BS;
+        const int x = e[c] / 9, z = e[c] - 9 * x;
+        e[c] = ev[c] ? e[c] : 0;
+        et[c] = ev[c] ? 9 * z + x : 0;
+    }
+    double t1 = 0.0, t2 = 0.0, n1 = 0.0, n2 = 0.0;
+    const int64_t p0 = rp[i], p1 = rp[i + 1];
+    for (int64_t pb = p0; pb < p1; pb += U) {
+        T xp[U][3], zp[U][3], xq[U][3], yq[U][3];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t p = pb + u;
+            const bool pv = p < p1;
+            const int64_t q = pv ? __ldg(tr + p) : 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const bool v = pv && ev[c];
+                xp[u][c] = v ? __ldg(X + p * BS + e[c]) : T(0);
+                zp[u][c] = v ? __ldg(Z + p * BS + e[c]) : T(0);
+                xq[u][c] = v ? __ldg(X + q * BS + et[c]) : T(0);
+                yq[u][c] = v ? __ldg(Y + q * BS + et[c]) : T(0);
+            }
+        }
+        // a lane's 12 products of the four blocks per trace in the value
+        // precision, then one FP64 addition
+        T a1 = T(0), a2 = T(0), a3 = T(0), a4 = T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                a1 = fma(xp[u][c], yq[u][c], a1);
+                a2 = fma(zp[u][c], yq[u][c], a2);
+                a3 = fma(xp[u][c], xq[u][c], a3);
+                a4 = fma(zp[u][c], xq[u][c], a4);
             }
         t1 += (double)a1;
         t2 += (double)a2;
@@ -270,15 +348,21 @@ lnv_status trace_rows(lnv_ctx *ctx, const lnv_pattern *P, int nsf, lnv_prec prec
         set_error("trace needs a symmetric pattern");
         return LNV_ERR_PATTERN;
     }
-    // the LNV four-trace pass {X, Z, X, Z} x {Y, Y, X, X} with 4x4 blocks
-    if (nterms == 4 && nsf == 4 && A[0] == A[2] && A[1] == A[3] && B[0] == B[1] && B[2] == B[3] &&
+    // the LNV four-trace pass {X, Z, X, Z} x {Y, Y, X, X} with 4x4 or 9x9 blocks
+    if (nterms == 4 && (nsf == 4 || nsf == 9) && A[0] == A[2] && A[1] == A[3] && B[0] == B[1] && B[2] == B[3] &&
         B[2] == A[0] && P->n > 0) {
         const unsigned grid = (unsigned)((P->n * 32 + 255) / 256);
-        if (prec == LNV_FP64)
+        if (nsf == 4 && prec == LNV_FP64)
             k_trace_lnv4<double><<<grid, 256, 0, ctx->stream>>>(P->n, P->row_ptr, P->tr, (const double *)A[0],
                                                                 (const double *)B[0], (const double *)A[1], row_part);
-        else
+        else if (nsf == 4)
             k_trace_lnv4<float><<<grid, 256, 0, ctx->stream>>>(P->n, P->row_ptr, P->tr, (const float *)A[0],
+                                                               (const float *)B[0], (const float *)A[1], row_part);
+        else if (prec == LNV_FP64)
+            k_trace_lnv9<double><<<grid, 256, 0, ctx->stream>>>(P->n, P->row_ptr, P->tr, (const double *)A[0],
+                                                                (const double *)B[0], (const double *)A[1], row_part);
+        else
+            k_trace_lnv9<float><<<grid, 256, 0, ctx->stream>>>(P->n, P->row_ptr, P->tr, (const float *)A[0],
                                                                (const float *)B[0], (const float *)A[1], row_part);
         LNV_LAUNCHED();
         return LNV_OK;
