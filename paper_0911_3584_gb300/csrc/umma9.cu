@@ -35,7 +35,7 @@
 // engine) of the 16-byte aligned span that holds it, a few per row instead
 // of one per block.
 //
-// Warp roles.  Two copy warps load the blocks' positions two stages ahead
+// Warp roles.  Four copy warps load the blocks' positions two stages ahead
 // (raw words in registers, decoded when used), write each block's
 // shared-memory offset to the slot's table and issue the copies; the slot's
 // "landed" barrier completes when every copy has arrived (bulk copies count
@@ -47,10 +47,11 @@
 // MMAs, one per accumulator.  kDA copy slots and two operand stages: copies
 // run up to kDA - 1 stages ahead of the stage being split.
 //
-// Measured on GB300 (Z = L T^T, 4096 atoms, NSF = 9): the pipeline is bound
-// by the copy warps' bulk-copy issue (about 30 requests of 1-2 KB per
-// stage); 16-byte cp.async pieces issued by the compute warps themselves, or
-// by more copy warps, and one bulk copy per block were each slower.
+// Measured on GB300 (Z = L T^T, 4096 atoms, NSF = 9): with the 21 rows of a
+// stage spread over four copy warps (two: 20% slower; six: no faster), the
+// copy warps' work and the compute warps' work take about 0.9 us per stage
+// each; 16-byte cp.async pieces issued by the compute warps themselves, or by
+// six copy warps, and one bulk copy per block were each slower.
 //
 // Every wait is bounded (mbarriers only, no named barriers): after a wait
 // runs out, the CTA-wide abort flag makes every other wait give up, the CTA
@@ -88,7 +89,10 @@ constexpr int kRowsA = kG;            // op(A) rows (rows m) per stage
 constexpr int kNQ = LNV_TC9_NQ;       // compute warps per TMEM lane quarter
 constexpr int kNPW = 4 * kNQ;         // compute warps (split, TMEM and B-operand stores)
 constexpr int kProd = kNPW * 32;      // compute threads
-constexpr int kCP = 2;                // copy warps (block positions, bulk copies)
+#ifndef LNV_TC9_CP
+#define LNV_TC9_CP 4
+#endif
+constexpr int kCP = LNV_TC9_CP;       // copy warps (block positions, bulk copies)
 constexpr int kCT = kCP * 32;         // copy threads
 constexpr int kMW = 3;                // MMA warps: hi*hi, lo*hi, hi*lo
 constexpr int kThreads = kProd + kCT + 32 * kMW;
@@ -295,19 +299,22 @@ k_umma9(const int2 *__restrict__ items, const int64_t *__restrict__ k_off, const
         __syncwarp();
     } else if (warp >= kNPW) {
         // ---------------------------------------------------------------- copy warps
-        // Per stage 21 rows of kKA blocks: op(B) row jt (blocks (kk, jt)), copied
-        // by lane jt of copy warp 0, and op(A) row m (blocks (kk, m)), by lane m
-        // of copy warp 1.  The present blocks of a row whose positions follow
-        // one another form a run, copied as one bulk copy (cp.async.bulk, the
-        // TMA engine) of the aligned span that holds it; each block's table
-        // entry is the float offset of its data in shared memory (the zero
-        // block when absent).  A run ending with an array's last block is cut
-        // at the last 16-byte boundary and its tail copied by a cp.async piece
-        // of the remaining bytes, so nothing past the array is read.
-        static_assert(kCP == 2, "copy split");
+        // Per stage 21 rows of kKA blocks: op(B) rows jt (blocks (kk, jt)) and
+        // op(A) rows m (blocks (kk, m)), one lane each: row gr (op(B) rows
+        // 0..13, then op(A) rows 14..20) goes to copy warp gr % kCP, lane
+        // gr / kCP.  The present blocks of a row whose positions follow one
+        // another form a run, copied as one bulk copy (cp.async.bulk, the TMA
+        // engine) of the aligned span that holds it; each block's table entry
+        // is the float offset of its data in shared memory (the zero block
+        // when absent).  A run ending with an array's last block is cut at the
+        // last 16-byte boundary and its tail copied by a cp.async piece of the
+        // remaining bytes, so nothing past the array is read.
+        static_assert((kRowsG + kRowsA + kCP - 1) / kCP <= 32, "copy split");
         const uint16_t *bx = bidx + bidx_off[g];
         const int cw = warp - kNPW;
-        const bool brow = cw == 0 && lane < kRowsG, arow = cw == 1 && lane < kRowsA;
+        const int gr = lane * kCP + cw;
+        const bool brow = gr < kRowsG, arow = gr >= kRowsG && gr < kRowsG + kRowsA;
+        const int rid = brow ? gr : gr - kRowsG;  // jt of an op(B) row, m of an op(A) row
         const bool has_row = brow || arow;
         const char *vbase = reinterpret_cast<const char *>(brow ? b_val : a_val);
         const int32_t last = brow ? b_last : a_last;
@@ -323,7 +330,7 @@ k_umma9(const int2 *__restrict__ items, const int64_t *__restrict__ k_off, const
             if (!has_row || ii >= nst) return;
             const int64_t k0 = (int64_t)ii * kKA;
             if (brow) {
-                const int64_t jl = j0 + lane;
+                const int64_t jl = j0 + rid;
                 if (jl >= nj) return;
                 if (TB) {
                     // four consecutive 16-bit offsets: one aligned 8-byte load
@@ -345,13 +352,13 @@ k_umma9(const int2 *__restrict__ items, const int64_t *__restrict__ k_off, const
             } else {
 #pragma unroll
                 for (int kk = 0; kk < kKA; ++kk)
-                    if (k0 + kk < nk) r.w[kk] = (uint32_t)__ldg(apos + (kb + k0 + kk) * kG + lane);
+                    if (k0 + kk < nk) r.w[kk] = (uint32_t)__ldg(apos + (kb + k0 + kk) * kG + rid);
             }
         };
         auto positions = [&](int ii, const Raw &r, int32_t (&p)[kKA]) {
             const int64_t k0 = (int64_t)ii * kKA;
             if (brow && TB) {
-                const int32_t r0 = jrow[lane];
+                const int32_t r0 = jrow[rid];
                 const uint32_t e[4] = {r.w[0] & 0xFFFFu, r.w[0] >> 16, r.w[1] & 0xFFFFu, r.w[1] >> 16};
 #pragma unroll
                 for (int kk = 0; kk < kKA; ++kk)
@@ -370,11 +377,11 @@ k_umma9(const int2 *__restrict__ items, const int64_t *__restrict__ k_off, const
             int32_t *tb = tbl + a * kNB;
             const uint32_t lb = landed_bar(a);
             if (has_row) {
-                const int row = brow ? lane : kRowsG + lane;
+                const int row = brow ? rid : kRowsG + rid;
                 uint32_t cur = s0 + (uint32_t)(kOffRaw + a * kRaw + row * kRowB);
 #pragma unroll
                 for (int kk = 0; kk < kKA; ++kk) {
-                    const int b = brow ? kk * kJT + lane : kNBG + kk * kG + lane;
+                    const int b = brow ? kk * kJT + rid : kNBG + kk * kG + rid;
                     // a run starts at kk when this block is present and its
                     // predecessor is absent or not adjacent in memory
                     if (pn[kk] < 0) {
@@ -394,7 +401,7 @@ k_umma9(const int2 *__restrict__ items, const int64_t *__restrict__ k_off, const
 #pragma unroll
                     for (int q = kk; q < kKA; ++q)
                         if (q - kk < n) {
-                            const int bq = brow ? q * kJT + lane : kNBG + q * kG + lane;
+                            const int bq = brow ? q * kJT + rid : kNBG + q * kG + rid;
                             tb[bq] = fo + 81 * (q - kk);
                         }
                     const bool tail = p0 + n - 1 == last && (span & 15u) != 0;
