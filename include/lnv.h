@@ -345,6 +345,18 @@ lnv_status lnv_energy_grad(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
                            const void *H_dev, const void *L_dev, double *out_dev,
                            void *G_dev, void *GN_dev, void *ws_dev, size_t ws_bytes);
 
+/* The same evaluation (Sec. 2, Eq. 3) from host memory: S_host, H_host and
+ * L_host (the layouts and symmetry of lnv_energy_grad) are copied to device
+ * buffers the system allocates on first use and keeps, the evaluation runs
+ * on the context stream with the system's own workspace, and out_host[6 s +
+ * 0..5] and, when G_host is not NULL, dE/dL are copied back.  Synchronises:
+ * the host arrays are read and written before the call returns.  Pinned
+ * (page-locked) host memory copies fastest; any host memory is accepted.
+ * Errors as lnv_energy_grad; LNV_ERR_OOM when the device buffers cannot be
+ * allocated. */
+lnv_status lnv_energy_grad_host(lnv_ctx *ctx, lnv_system *sys, const void *S_host, const void *H_host,
+                                const void *L_host, double *out_host, void *G_host);
+
 /* ------------------------------------------------------------------ minimisation
  * The search for the ground state around the evaluation: vary L on its
  * pattern to minimise the energy with the electron count set (Sec. 2,

@@ -88,6 +88,8 @@ struct lnv_system {
     int64_t *sub_lt = nullptr;  // position in P_t of every block of P_l
     void *own_ws = nullptr;
     size_t own_ws_bytes = 0;
+    // device copies of the host arrays of lnv_energy_grad_host (allocated on first use)
+    void *io_dev = nullptr;
     // stage timing (lnv_system_profile): events before XY, TU, Z, traces, Q, W, G and at the end
     static constexpr int kStages = 7;
     int profile = 0;
@@ -141,6 +143,7 @@ void system_free(lnv_system *s)
     cudaFree(s->sub_lt);
     cudaFree(s->seg_off_dev);
     cudaFree(s->own_ws);
+    cudaFree(s->io_dev);
     for (auto &e : s->ev)
         if (e) cudaEventDestroy(e);
     delete s;
@@ -697,6 +700,38 @@ lnv_status lnv_system_stage_ms(lnv_system *sys, double *ms)
             ms[k] = f;
         }
     }
+    return LNV_OK;
+}
+
+lnv_status lnv_energy_grad_host(lnv_ctx *ctx, lnv_system *sys, const void *S_host, const void *H_host,
+                                const void *L_host, double *out_host, void *G_host)
+{
+    LNV_TRY(set_dev(ctx));
+    LNV_ARG(sys && S_host && H_host && L_host && out_host, "null pointer");
+    const size_t bs = (size_t)sys->nsf * sys->nsf * elem_size(sys->prec);
+    const size_t n_sh = align256(bs * (size_t)sys->P_sh->nnzb), n_l = align256(bs * (size_t)sys->P_l->nnzb);
+    const size_t n_out = align256(sizeof(double) * 6 * (size_t)sys->n_seg);
+    if (!sys->io_dev) {
+        // S, H, L, G, out, each on a 256-byte boundary
+        cudaError_t e = cudaMalloc(&sys->io_dev, 2 * n_sh + 2 * n_l + n_out);
+        if (e != cudaSuccess) {
+            sys->io_dev = nullptr;
+            set_error("host-evaluation buffers: %s", cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? LNV_ERR_OOM : LNV_ERR_CUDA;
+        }
+    }
+    unsigned char *b = (unsigned char *)sys->io_dev;
+    void *S = b, *H = b + n_sh, *L = b + 2 * n_sh, *G = b + 2 * n_sh + n_l;
+    double *out = (double *)(b + 2 * n_sh + 2 * n_l);
+    const size_t v_sh = bs * (size_t)sys->P_sh->nnzb, v_l = bs * (size_t)sys->P_l->nnzb;
+    LNV_CUDA(cudaMemcpyAsync(S, S_host, v_sh, cudaMemcpyHostToDevice, ctx->stream));
+    LNV_CUDA(cudaMemcpyAsync(H, H_host, v_sh, cudaMemcpyHostToDevice, ctx->stream));
+    LNV_CUDA(cudaMemcpyAsync(L, L_host, v_l, cudaMemcpyHostToDevice, ctx->stream));
+    LNV_TRY(lnv_energy_grad(ctx, sys, S, H, L, out, G_host ? G : nullptr, nullptr, nullptr, 0));
+    LNV_CUDA(cudaMemcpyAsync(out_host, out, sizeof(double) * 6 * (size_t)sys->n_seg, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    if (G_host) LNV_CUDA(cudaMemcpyAsync(G_host, G, v_l, cudaMemcpyDeviceToHost, ctx->stream));
+    LNV_CUDA(cudaStreamSynchronize(ctx->stream));
     return LNV_OK;
 }
 

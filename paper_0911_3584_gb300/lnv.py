@@ -71,6 +71,7 @@ def lib():
                 "lnv_system_triples": [P, i32, P],
                 "lnv_system_destroy": [P],
                 "lnv_energy_grad": [P, P, P, P, P, P, P, P, P, ctypes.c_size_t],
+                "lnv_energy_grad_host": [P, P, P, P, P, P, P],
                 "lnv_system_profile": [P, i32],
                 "lnv_system_stage_ms": [P, P],
                 "lnv_system_stage_triples": [P, P],
@@ -457,6 +458,29 @@ class System:
                "lnv_energy_grad")
         if grad_ne:
             return out, (G if grad else None), GN
+        return out, (G if grad else None)
+
+    def energy_grad_host(self, S, H, L, grad: bool = True, out=None, G=None):
+        """One evaluation from host memory (lnv_energy_grad_host: the library
+        copies S, H, L in and the results out, and synchronises).  S, H, L are
+        contiguous CPU tensors in the system's precision (pinned ones copy
+        fastest); returns (out [n_seg, 6] FP64 CPU tensor, G CPU tensor or None)."""
+        def host(t, pattern, name):
+            if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+                raise ValueError(f"{name} must be a CPU tensor")
+            if t.dtype != DTYPE[self.prec] or t.numel() != pattern.nnzb * self.nsf * self.nsf \
+                    or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous {DTYPE[self.prec]} tensor of "
+                                 f"{pattern.nnzb} blocks of {self.nsf}x{self.nsf}")
+            return ctypes.c_void_p(t.data_ptr())
+        s, h, l_ = host(S, self.P_sh, "S"), host(H, self.P_sh, "H"), host(L, self.P_l, "L")
+        if out is None:
+            out = torch.empty((self.n_seg, 6), dtype=torch.float64)
+        if grad and G is None:
+            G = torch.empty(L.shape, dtype=L.dtype)
+        g = host(G, self.P_l, "G") if grad else ctypes.c_void_p(None)
+        _check(lib().lnv_energy_grad_host(self.ctx.h, self.h, s, h, l_, ctypes.c_void_p(out.data_ptr()), g),
+               "lnv_energy_grad_host")
         return out, (G if grad else None)
 
     STAGES = ("XY", "TU", "Z", "traces", "Q", "W", "G")

@@ -587,6 +587,27 @@ def test_32768_atoms_sampled_rows_bench_configuration(ctx, nsf):
         assert abs(o32[1] - o64[1]) <= TOL[torch.float32][1] * abs(o64[1]), (o32[1], o64[1])
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_energy_grad_from_host_buffers(ctx, dtype, pinned):
+    """lnv_energy_grad_host (host arrays in, results in host memory) gives the
+    device-pointer evaluation's results bit for bit, with pinned or pageable
+    host memory, with and without the gradient; against the oracle too."""
+    w, S, H, L = workload(2, 4, 6.6, 8.0, seed=12)
+    sysm = System(ctx, 4, PREC[dtype], w["pos"], w["cell"], 6.6, 8.0)
+    hs = [torch.from_numpy(np.ascontiguousarray(w[k])).to(dtype) for k in ("S", "H", "L")]
+    if pinned:
+        hs = [t.pin_memory() for t in hs]
+    out_h, G_h = sysm.energy_grad_host(*hs)
+    assert out_h.device.type == "cpu" and G_h.device.type == "cpu"
+    out_d, G_d = sysm.energy_grad(*(t.to(ctx.device) for t in hs))
+    assert torch.equal(out_h, out_d.cpu()) and torch.equal(G_h, G_d.cpu())
+    out_e, G_e = sysm.energy_grad_host(*hs, grad=False)
+    assert G_e is None and torch.equal(out_e[:, :2], out_h[:, :2])
+    ref = oracle_lnv(w, rounded(S, dtype), rounded(H, dtype), rounded(L, dtype))
+    _check_lnv(out_h.numpy(), G_h.numpy(), ref, dtype)
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_autotuned_system_matches_oracle(ctx, dtype):
     """After the autotuner picks a kernel per product, results still match."""
