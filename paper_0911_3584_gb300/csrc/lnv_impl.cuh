@@ -134,7 +134,7 @@ constexpr int kTc9G = 7;
 constexpr int kTc9Cols = 14;
 
 // Triple-list plan of a product (see triples.cu): C's blocks as work items,
-// ordered by groups of 4 rows, then column, then row inside the group; for
+// ordered by groups of 4 rows, then by list length inside the group; for
 // each item the contributing (op(A)_ik, op(B)_kj) storage positions, k
 // ascending.
 struct TriplePlan {

@@ -1125,8 +1125,9 @@ k_gw(const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
 // op(B)_kj (the group's four lanes read the same addresses) and adds their
 // product; the next pair's blocks are fetched while the current ones are
 // applied.  Nothing is multiplied that is absent or discarded.  Items are
-// ordered by groups of four rows, then column, so the warps that run together
-// share most blocks and hit in L1.  With sub (not null) the launch covers the
+// ordered by groups of four rows, then by list length, so a warp's eight
+// items end together and its lanes stay busy (the FP64 pipe spends a full
+// slot on a partly idle warp instruction).  With sub (not null) the launch covers the
 // items sub[0 .. n_items - 1] only (the upper triangle of a symmetric output).
 template <typename T, int NOUT, bool TA, bool TB>
 __global__ void __launch_bounds__(128)

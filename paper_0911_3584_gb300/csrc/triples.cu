@@ -4,11 +4,15 @@
 // op(A)_ik and op(B)_kj stored.  This pass lists, once per plan, those pairs
 // of storage positions for every block of C, k ascending, so the numeric
 // kernel neither searches B's rows nor multiplies blocks that are absent.
-// The blocks of C are ordered by groups of four consecutive rows, then by
-// column, then by row inside the group: the threads that run together then
-// share most blocks of A (same row) and of B (same column), and those reads
-// hit in L1.
+// The blocks of C are ordered by groups of four consecutive rows, and inside
+// a group by the length of their lists, longest first (ties: by column, then
+// row).  The numeric kernel runs eight blocks per warp and a warp lasts as
+// long as its longest list, so lists of like length keep its lanes busy: on
+// the products whose lists vary with the distance |r_i - r_j| (T = SX, U = SY
+// and X = LS, Y = LH), column order left a third of the lanes idle.  Every
+// block still sums its own list in k order, so the order changes no result.
 #include <algorithm>
+#include <cstdint>
 #include <thread>
 #include <vector>
 
@@ -82,7 +86,8 @@ lnv_status triple_plan_build(lnv_ctx *ctx, lnv_plan *pl, size_t budget_bytes)
         set_error("triple-list plan needs %zu bytes, over the %zu budget", need, budget_bytes);
         return LNV_ERR_UNSUPPORTED;
     }
-    // item order: groups of rows, then column, then row (host, from C's pattern)
+    // first order: groups of rows, then column, then row (host, from C's
+    // pattern); the lengths counted in this order then reorder each group
     LNV_TRY(pattern_host_cols(ctx, C));
     const int64_t n = C->n, G = kTripleGroup, ng = (n + G - 1) / G;
     std::vector<int32_t> items((size_t)C->nnzb);
@@ -137,6 +142,43 @@ lnv_status triple_plan_build(lnv_ctx *ctx, lnv_plan *pl, size_t budget_bytes)
                                                nullptr, nullptr);
         if (cudaGetLastError() != cudaSuccess) s = LNV_ERR_CUDA;
         count_launch();
+    }
+    if (s == LNV_OK && C->nnzb > 0) {
+        // order each group's items by list length, longest first (stable:
+        // equal lengths keep the column order), and the counts with them
+        std::vector<int64_t> c_h((size_t)C->nnzb), c_o((size_t)C->nnzb);
+        if (cudaMemcpyAsync(c_h.data(), cnt, sizeof(int64_t) * c_h.size(), cudaMemcpyDeviceToHost,
+                            ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            s = LNV_ERR_CUDA;
+        } else {
+            std::vector<int32_t> sorted(items.size());
+            const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+            std::vector<std::thread> th;
+            for (int t = 0; t < nth; ++t)
+                th.emplace_back([&, t] {
+                    std::vector<int64_t> ord;
+                    for (int64_t g = t; g < ng; g += nth) {
+                        const int64_t q0 = C->h_row_ptr[g * G], q1 = C->h_row_ptr[std::min(n, g * G + G)];
+                        ord.resize((size_t)(q1 - q0));
+                        for (int64_t q = q0; q < q1; ++q) ord[(size_t)(q - q0)] = q;
+                        std::stable_sort(ord.begin(), ord.end(),
+                                         [&](int64_t a, int64_t b) { return c_h[(size_t)a] > c_h[(size_t)b]; });
+                        for (int64_t q = q0; q < q1; ++q) {
+                            sorted[(size_t)q] = items[(size_t)ord[(size_t)(q - q0)]];
+                            c_o[(size_t)q] = c_h[(size_t)ord[(size_t)(q - q0)]];
+                        }
+                    }
+                });
+            for (auto &x : th) x.join();
+            items.swap(sorted);
+            if (cudaMemcpyAsync(tp.item_cb, items.data(), sizeof(int32_t) * items.size(), cudaMemcpyHostToDevice,
+                                ctx->stream) != cudaSuccess ||
+                cudaMemcpyAsync(cnt, c_o.data(), sizeof(int64_t) * c_o.size(), cudaMemcpyHostToDevice,
+                                ctx->stream) != cudaSuccess ||
+                cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+                s = LNV_ERR_CUDA;
+        }
     }
     if (s == LNV_OK) s = scan_exclusive(ctx->stream, cnt, C->nnzb, tp.t_off);
     int64_t total = 0;
