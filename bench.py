@@ -36,7 +36,9 @@ STAGE_KERNEL = {"XY": "X=LS, Y=LH", "TU": "T=SX, U=SY", "Z": "Z=L T^T", "Q": "Q=
 KERNEL_NAME = {"push": "k_push2", "pull": "k_pull", "pull-merge": "k_pull2", "group": "k_grp",
                "group-sparse": "k_grp (hit lists)", "group-pipe": "k_gw", "group-mma": "k_gmma",
                "triples": "k_tri", "group-pipe-half": "k_gw (half-width slices)",
-               "tensor": "k_umma (tcgen05, 3xTF32)", "tensor9": "k_umma9 (tcgen05, 3xTF32, NSF = 9)"}
+               "tensor": "k_umma (tcgen05, 3xTF32)", "tensor9": "k_umma9 (tcgen05, 3xTF32, NSF = 9)",
+               "tensor-tile": "k_umma_tile (tcgen05, 3xTF32, per-tile k lists)"}
+TENSOR_KERNELS = ("tensor", "tensor9", "tensor-tile")
 
 
 def parse():
@@ -140,7 +142,8 @@ class Clocks:
 
 def product_source_sha():
     h = hashlib.sha1()
-    for f in ("mult_kernels.cuh", "mult.cu", "umma.cu", "umma9.cu", "tcgen05.cuh", "group.cu", "triples.cu"):
+    for f in ("mult_kernels.cuh", "mult.cu", "umma.cu", "umma9.cu", "umma_tile.cu", "tcgen05.cuh", "group.cu",
+              "triples.cu"):
         with open(os.path.join(ROOT, "paper_0911_3584_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -268,7 +271,7 @@ def roofline_tensor(res):
     tf32 = pk["bf16_tflops"] / 2.0
     out = []
     for st, k in res["kernels"].items():
-        if k != "tensor" or res["stage_ms"].get(st, 0) <= 0:
+        if k not in TENSOR_KERNELS or res["stage_ms"].get(st, 0) <= 0:
             continue
         ms = res["stage_ms"][st]
         achieved = res["flops_stage"][st] / (ms * 1e-3) / 1e12
@@ -665,7 +668,7 @@ def run_large(args, ctx, nsf, r_l, autograd):
     st_tr = sysm.stage_triples()
     tensor_stages = []
     for st, (k, ms) in tuned.items():
-        if k in ("tensor", "tensor9") and ms > 0:
+        if k in TENSOR_KERNELS and ms > 0:
             ach = 2 * nsf ** 3 * st_tr[st] / (ms * 1e-3) / 1e12
             tensor_stages.append({"stage": st, "kernel": KERNEL_NAME.get(k, k), "bound": "tensor",
                                   "achieved": round(ach, 3), "peak": round(pk["bf16_tflops"] / 2, 1),

@@ -193,15 +193,21 @@ lnv_status lnv_plan_product(lnv_ctx *ctx, const lnv_pattern *A, const lnv_patter
  * 4 (other cases run kernel 0), 10 the same for 9 x 9 blocks: row groups of
  * 7 atoms (N = 63 of 64), 128-row tiles of 14 output columns (M = 126 of
  * 128), K in stages of 8 k-atoms; either op(B); FP32 values with NSF = 9
- * (other cases run kernel 0); value arrays 16-byte aligned (else
- * LNV_ERR_UNSUPPORTED from the multiply).
+ * (other cases run kernel 0), 11 kernel 9's 8-row groups and tcgen05
+ * pipeline taken one 128-row tile (32 output columns) at a time over only
+ * the k's at which one of the tile's columns holds op(B)_kj, for the tables
+ * that are sparse as a whole but dense per tile (T = SX, U = SY); either
+ * op(B); a symmetric first output is formed on the tiles of its upper part
+ * and mirrored; FP32 values with NSF = 4 (other cases run kernel 0).
+ * Kernels 9-11 need value arrays 16-byte aligned (else LNV_ERR_UNSUPPORTED
+ * from the multiply).
  * The default is 3 when at least half of the table's candidates hit, else 4,
  * when the tables fit a third of the free device memory. */
 lnv_status lnv_plan_info(const lnv_plan *plan, int64_t *triples, int *mode);
 /* Number of product kernels (0 .. LNV_NUM_KERNELS - 1). */
-#define LNV_NUM_KERNELS 11
-/* Select the kernel of a plan (0..10 as above); all give the same result up
- * to rounding order.  Kernels 3-10 build their tables on first selection
+#define LNV_NUM_KERNELS 12
+/* Select the kernel of a plan (0..11 as above); all give the same result up
+ * to rounding order.  Kernels 3-11 build their tables on first selection
  * (allocates, synchronises).  LNV_ERR_UNSUPPORTED if the kernel cannot run
  * this plan. */
 lnv_status lnv_plan_set_kernel(lnv_ctx *ctx, lnv_plan *plan, int kernel);

@@ -602,12 +602,14 @@ lnv_status lnv_system_autotune(lnv_ctx *ctx, lnv_system *sys, const void *S_dev,
         // triangle, then the mirror) and without (formed whole)
         for (int split = sg.pl->sym1; split >= 0 && st == LNV_OK; --split) {
             st = plan_set_split(ctx, sg.pl, split);
-            for (int k : {0, 2, 3, 4, 5, 8, 6, 7, 9, 10}) {
+            for (int k : {0, 2, 3, 4, 5, 8, 6, 7, 9, 10, 11}) {
                 if (st != LNV_OK) break;
                 // tcgen05 kernel: one FP32 product with NSF = 4 and op(B) = B^T
                 if (k == 9 && (sys->nsf != 4 || sys->prec != LNV_FP32 || !sg.pl->trans_b || sg.B2)) continue;
                 // its NSF = 9 form: FP32 products with NSF = 9
                 if (k == 10 && (sys->nsf != 9 || sys->prec != LNV_FP32)) continue;
+                // tcgen05 tiles over their own k lists: FP32 products with NSF = 4
+                if (k == 11 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
                 // per-warp ring kernel: FP32 values, NSF = 4 (elsewhere kernel 5 is kernel 3)
                 if (k == 5 && (sys->nsf != 4 || sys->prec != LNV_FP32)) continue;
                 // its half-width form: the same cases

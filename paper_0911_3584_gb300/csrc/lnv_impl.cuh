@@ -133,6 +133,29 @@ constexpr int kTcCols = 64;
 constexpr int kTc9G = 7;
 constexpr int kTc9Cols = 14;
 
+// Tile plan of kernel 11 (umma_tile.cu), built from the 8-row tables in tc:
+// one work item per 32 columns of a group's J, with the item's own k list
+// (the k's at which any of its columns holds op(B)_kj, padded with empty
+// entries to a multiple of 4).  Per listed k: B's row start (block index of
+// row k; op(B) = B only) and the op(A) positions of the group's 8 rows; per
+// item a j-major table of 16-bit offsets of op(B)_kj in its stored row
+// (0xFFFF: absent), [32 columns][its k count].
+struct TilePlan {
+    int64_t n_items = 0;
+    int2 *items = nullptr;       // [n_items] (group, first column of J)
+    int64_t *ck_off = nullptr;   // [n_items + 1] the item's range of listed k's
+    int32_t *ck_brow = nullptr;  // [listed]
+    int32_t *ck_apos = nullptr;  // [listed][8]
+    uint16_t *ck_tab = nullptr;  // [listed * 32]
+    // plans with a symmetric first output: the items holding a column j >=
+    // the group's first row (the first output formed on its upper triangle)
+    int32_t *up = nullptr;
+    int64_t n_up = 0;
+    int64_t listed = 0;
+    const int2 *src = nullptr;   // tc.items the plan was built from
+    size_t bytes = 0;
+};
+
 // Triple-list plan of a product (see triples.cu): C's blocks as work items,
 // ordered by groups of 4 rows, then by list length inside the group; for
 // each item the contributing (op(A)_ik, op(B)_kj) storage positions, k
@@ -161,10 +184,13 @@ struct lnv_plan {
     // 3 row groups with a dense position table, 4 row groups with hit lists,
     // 5 row groups with per-warp lists, 6 row groups on tensor cores, 7
     // listed triples per output block, 8 kernel 5 with warp slices of half
-    // the width, 9 8-row groups on the tcgen05 tensor cores (tables in tc)
+    // the width, 9 8-row groups on the tcgen05 tensor cores (tables in tc),
+    // 10 its NSF = 9 form, 11 tcgen05 tiles of 32 columns over their own k
+    // lists (tables in tc and tt)
     int mode;
     GroupPlan grp;
-    GroupPlan tc;  // 8-row groups of the tensor-core kernel (9)
+    GroupPlan tc;  // 8-row groups of the tensor-core kernels (9, 11; 7-row groups for 10)
+    TilePlan tt;   // kernel 11's per-tile k lists
     TriplePlan tri;
     // work items (row, first output slot) of the merge-join pull, for 64 and
     // 128 outputs per CTA (device arrays)
@@ -227,6 +253,16 @@ lnv_status umma_prepare(lnv_ctx *ctx, lnv_plan *pl);
 // Kernel 10 (umma9.cu): C = mask(op(A) op(B)) on 7-row groups, tcgen05 tensor
 // cores, FP32 values, NSF = 9.
 lnv_status launch_umma9(lnv_ctx *ctx, const lnv_plan *pl, bool ta, bool tb, const void *A, const void *B, void *C);
+// Kernel 11 (umma_tile.cu): C = mask(op(A) op(B)) on 32-column tiles of
+// 8-row groups over each tile's own k list, tcgen05 tensor cores, FP32
+// values, NSF = 4, either op(B).  upper: only the tiles holding a column j >=
+// the group's first row (a symmetric output formed on its upper triangle).
+lnv_status launch_umma_tile(lnv_ctx *ctx, const lnv_plan *pl, bool ta, bool tb, bool upper, const void *A,
+                            const void *B, void *C);
+// Build kernel 11's tile plan from the plan's 8-row tables (tc, finished by
+// umma_prepare); LNV_ERR_UNSUPPORTED over the budget.
+lnv_status tile_plan_build(lnv_ctx *ctx, lnv_plan *pl, size_t budget_bytes);
+void tile_plan_free(TilePlan *tt);
 lnv_status scan_exclusive(cudaStream_t st, const int64_t *in, int64_t n, int64_t *out);
 void group_plan_free(GroupPlan *gp);
 // Triple-list plan (triples.cu); LNV_ERR_UNSUPPORTED when it would not fit the budget.

@@ -274,7 +274,7 @@ lnv_status plan_pull_items(lnv_plan *pl)
 
 lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
 {
-    LNV_ARG(pl && kernel >= 0 && kernel < LNV_NUM_KERNELS, "kernel must be 0..10");
+    LNV_ARG(pl && kernel >= 0 && kernel < LNV_NUM_KERNELS, "kernel must be 0..11");
     if (kernel == 2) {
         if (!pl->B->symmetric) {
             set_error("the merge-join pull needs a symmetric B pattern");
@@ -297,8 +297,16 @@ lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
         // 7-row group tables with the dense position table (either op(B))
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        tile_plan_free(&pl->tt);
         LNV_TRY(group_plan_build_into(ctx, pl, kTc9G, free_b / 3, true, false, pl->tc));
         LNV_TRY(umma_prepare(ctx, pl));
+    } else if (kernel == 11) {
+        // kernel 9's 8-row tables (either op(B)), then each 32-column tile's k list
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        LNV_TRY(group_plan_build_into(ctx, pl, 8, free_b / 3, true, false, pl->tc));
+        LNV_TRY(umma_prepare(ctx, pl));
+        LNV_TRY(tile_plan_build(ctx, pl, free_b / 3));
     } else if (kernel == 7) {
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
@@ -331,7 +339,8 @@ lnv_status plan_set_split(lnv_ctx *ctx, lnv_plan *pl, int on)
 void plan_trim(lnv_plan *plan)
 {
     if (plan->mode != 7) triple_plan_free(&plan->tri);
-    if (plan->mode != 9 && plan->mode != 10) group_plan_free(&plan->tc);
+    if (plan->mode != 9 && plan->mode != 10 && plan->mode != 11) group_plan_free(&plan->tc);
+    if (plan->mode != 11) tile_plan_free(&plan->tt);
     GroupPlan &gp = plan->grp;
     const bool dense = plan->mode == 3 || plan->mode == 5 || plan->mode == 6 || plan->mode == 8,
                sparse = plan->mode == 4;
@@ -355,6 +364,7 @@ void plan_free(lnv_plan *plan)
     cudaFree(plan->items64);
     cudaFree(plan->items128);
     group_plan_free(&plan->grp);
+    tile_plan_free(&plan->tt);
     group_plan_free(&plan->tc);
     triple_plan_free(&plan->tri);
     delete plan;

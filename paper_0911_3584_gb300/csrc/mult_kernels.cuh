@@ -1666,6 +1666,19 @@ lnv_status dispatch_mode(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const 
             return launch_push2<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, pl->sym1 && pl->split);
         }
     }
+    if (pl->mode == 11) {
+        // tcgen05 tiles over their own k lists: FP32 values, NSF = 4, either
+        // transpose; a symmetric first output on the tiles of its upper part
+        // (mirrored by the caller); other cases run the push kernel
+        if constexpr (NSF == 4 && sizeof(T) == 4) {
+            LNV_TRY(launch_umma_tile(ctx, pl, TA, TB, pl->sym1 && pl->split, A, B1, C1));
+            if (B2) LNV_TRY(launch_umma_tile(ctx, pl, TA, TB, false, A, B2, C2));
+            return LNV_OK;
+        } else {
+            if (B2) return launch_push2<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, pl->sym1 && pl->split);
+            return launch_push2<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, pl->sym1 && pl->split);
+        }
+    }
     if (pl->mode == 7) {
         if constexpr (NSF == 4) {
             // two fused FP32 products; FP64 runs them one at a time (registers)

@@ -124,7 +124,7 @@ def _set_kernel_or_refused(plan, kernel, tb):
 
 @pytest.mark.parametrize("kernel", ["default", "push", "pull", "pull-merge", "group", "group-sparse",
                                     "group-pipe", "group-mma", "triples", "group-pipe-half", "tensor",
-                                    "tensor9"])
+                                    "tensor9", "tensor-tile"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("nsf", [1, 2, 4, 9])
 @pytest.mark.parametrize("case", PRODUCT_CASES)
@@ -149,7 +149,8 @@ def test_masked_product_matches_oracle(ctx, dtype, nsf, case, kernel):
 
 
 @pytest.mark.parametrize("kernel", ["default", "push", "pull", "pull-merge", "group", "group-sparse",
-                                    "group-pipe", "group-mma", "triples", "group-pipe-half", "tensor9"])
+                                    "group-pipe", "group-mma", "triples", "group-pipe-half", "tensor9",
+                                    "tensor-tile"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("nsf", [1, 4, 9])
 def test_symmetric_product_formed_on_one_triangle(ctx, dtype, nsf, kernel):
@@ -257,7 +258,7 @@ def test_plan_modes_follow_symbolic_counts(ctx):
     assert e.value.status == -5
 
 
-@pytest.mark.parametrize("kernel", ["default", "tensor"])
+@pytest.mark.parametrize("kernel", ["default", "tensor", "tensor-tile"])
 @pytest.mark.parametrize("n_atoms", [1, 7, 9, 42, 131])
 def test_transposed_product_ragged_groups(ctx, kernel, n_atoms):
     """op(B) = B^T products on atom counts that leave a partial last row group
@@ -302,6 +303,50 @@ def test_tensor9_product_ragged_groups(ctx, n_atoms):
                               to_dev(B["val"], torch.float32, ctx.device))
             ref = oracle.mprod(oracle.transpose(A) if ta else A, oracle.transpose(B) if tb else B, oc)
             assert rel_fro(C.cpu().numpy(), ref["val"]) <= TOL[torch.float32][0], (ta, tb)
+    assert ctx.device_status() == 0
+
+
+@pytest.mark.parametrize("n_atoms", [1, 7, 8, 9, 33, 42, 131])
+def test_tensor_tile_product_ragged_groups(ctx, n_atoms):
+    """Kernel 11 (tiles of 32 columns over their own k lists) on atom counts
+    that leave a partial last 8-row group, partial tiles and tiles with few
+    listed k's, random clustered positions, every operand transpose: FP32
+    against the oracle."""
+    rng = np.random.default_rng(200 + n_atoms)
+    cell = np.array([20.0, 20.0, 20.0])
+    pos = rng.uniform(0, 9.0, size=(n_atoms, 3))
+    ra, rb, rc = 4.0, 7.0, 6.0
+    PA, PB, PC = (Pattern.build(ctx, pos, cell, r) for r in (ra, rb, rc))
+    oa, ob, oc = (oracle.pattern(pos, cell, r) for r in (ra, rb, rc))
+    A = rounded(oracle.csr(*oa, rng.standard_normal((oa[1].size, 4, 4))), torch.float32)
+    B = rounded(oracle.csr(*ob, rng.standard_normal((ob[1].size, 4, 4))), torch.float32)
+    for ta in (False, True):
+        for tb in (False, True):
+            plan = Plan(ctx, PA, PB, PC, trans_a=ta, trans_b=tb)
+            plan.set_kernel("tensor-tile")
+            C = plan.multiply(to_dev(A["val"], torch.float32, ctx.device),
+                              to_dev(B["val"], torch.float32, ctx.device))
+            ref = oracle.mprod(oracle.transpose(A) if ta else A, oracle.transpose(B) if tb else B, oc)
+            assert rel_fro(C.cpu().numpy(), ref["val"]) <= TOL[torch.float32][0], (ta, tb)
+    assert ctx.device_status() == 0
+
+
+def test_tensor_tile_repeated_calls_are_identical(ctx):
+    """Kernel 11 sums in a fixed order: two launches of T = S X (op(B) = B)
+    give bit-identical output, within the FP32 bound of the oracle."""
+    w, S, H, L = workload(3, 4, 6.6, 8.0, seed=7)
+    pos, cell = w["pos"], w["cell"]
+    PS, PX, PT = (Pattern.build(ctx, pos, cell, r) for r in (6.6, 14.6, 21.2))
+    ox = oracle.pattern(pos, cell, 14.6)
+    X = rounded(oracle.csr(*ox, np.random.default_rng(4).standard_normal((ox[1].size, 4, 4))), torch.float32)
+    plan = Plan(ctx, PS, PX, PT)
+    plan.set_kernel("tensor-tile")
+    Sd, Xd = to_dev(S["val"], torch.float32, ctx.device), to_dev(X["val"], torch.float32, ctx.device)
+    c1 = plan.multiply(Sd, Xd).cpu().numpy()
+    c2 = plan.multiply(Sd, Xd).cpu().numpy()
+    assert np.array_equal(c1, c2)
+    ref = oracle.mprod(rounded(S, torch.float32), X, oracle.pattern(pos, cell, 21.2))
+    assert rel_fro(c1, ref["val"]) <= TOL[torch.float32][0]
     assert ctx.device_status() == 0
 
 
@@ -525,12 +570,31 @@ def test_lnv_nsf9_tensor_core_products(ctx, ncell):
     assert ctx.device_status() == 0
 
 
-def test_lnv_4096_atoms_tensor_core_products(ctx, si4096):
-    """The benchmark workload with Z and W on the tcgen05 kernel."""
+@pytest.mark.parametrize("mirror", [True, False])
+def test_lnv_512_atoms_tensor_tile_products(ctx, si512, mirror):
+    """FP32 evaluation with every product stage on kernel 11 (T on the tiles of
+    its upper part and mirrored, or formed whole), every output against the
+    FP64 oracle at the FP32 bound."""
+    w, ref = si512
+    sysm = System(ctx, 4, "fp32", w["pos"], w["cell"], 6.6, 8.0)
+    for st in ("XY", "TU", "Z", "Q", "W"):
+        sysm.set_stage_kernel(st, "tensor-tile")
+    assert all(k == "tensor-tile" for k in sysm.stage_kernels().values())
+    sysm.set_mirror(mirror)
+    _, out, G = _gpu_lnv(ctx, w, torch.float32, sysm=sysm)
+    _check_lnv(out, G, ref, torch.float32)
+    assert ctx.device_status() == 0
+
+
+@pytest.mark.parametrize("tu", ["group-pipe", "tensor-tile"])
+def test_lnv_4096_atoms_tensor_core_products(ctx, si4096, tu):
+    """The benchmark workload with Z and W on the tcgen05 kernel 9 and TU on
+    the SIMT kernel or on kernel 11."""
     w, ref = si4096
     sysm = System(ctx, 4, "fp32", w["pos"], w["cell"], 6.6, 8.0)
     sysm.set_stage_kernel("Z", "tensor")
     sysm.set_stage_kernel("W", "tensor")
+    sysm.set_stage_kernel("TU", tu)
     _, out, G = _gpu_lnv(ctx, w, torch.float32, sysm=sysm)
     _check_lnv(out, G, ref, torch.float32)
     assert ctx.device_status() == 0
