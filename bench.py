@@ -246,6 +246,8 @@ def time_path(ctx, w, prec, steps, warmup, dist, kernels=None):
         "t_mirrored": sysm.mirror,
         "tensors": (S, H, L, out, G, ws),
         "setup": setup,
+        # the autotuner's timing of every applicable kernel per stage (None when pinned)
+        "tune": getattr(sysm, "tune_table", None),
     }
     return res
 
@@ -285,25 +287,39 @@ def roofline_tensor(res):
 
 
 def roofline(res, fma_tflops=None):
+    """The dominant product stage (by measured time) against the peak of the
+    pipe its kernel runs on: the dense TF32 tensor peak for the tcgen05
+    kernels (three TF32 passes per product, one-pass algorithmic flops
+    counted), else the FMA pipe of the precision.  The FMA probe's fraction
+    is given either way, to compare with the SIMT kernels."""
     prec = res["prec"]
-    # dominant product kernel by measured time
     cand = {k: v for k, v in res["stage_ms"].items() if k in STAGE_KERNEL and v > 0}
     stage = max(cand, key=cand.get)
     ms = cand[stage]
     achieved = res["flops_stage"][stage] / (ms * 1e-3) / 1e12
-    peak = PEAK_TFLOPS[prec]
-    tr = ncu_traffic(stage, prec)
-    return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 3), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": tr,
-            "kernel": f"{KERNEL_NAME[res['kernels'][stage]]} ({STAGE_KERNEL[stage]})"
-                      + (" on T's upper triangle, then k_mirror_lower" if stage == "TU" and res["t_mirrored"]
-                         else ""),
-            "stage": stage, "kernel_ms": round(ms, 4),
-            "algorithmic_flops_per_launch": res["flops_stage"][stage],
-            "peak_source": ("derived: 152 SMs x 2.07 GHz x 256 flop/clk/SM (FP32 FMA)" if prec == "fp32"
-                            else "nominal GB300 FP64 rate 1.25 TFLOP/s"),
-            "peak_fma_probe": round(fma_tflops, 3) if fma_tflops else None,
-            "frac_of_fma_probe": round(achieved / fma_tflops, 4) if fma_tflops else None}
+    kern = res["kernels"][stage]
+    out = {"bound": "alu", "achieved": round(achieved, 4), "unit": "TFLOP/s",
+           "traffic": ncu_traffic(stage, prec),
+           "kernel": f"{KERNEL_NAME[kern]} ({STAGE_KERNEL[stage]})"
+                     + (" on T's upper triangle, then k_mirror_lower" if stage == "TU" and res["t_mirrored"]
+                        else ""),
+           "stage": stage, "kernel_ms": round(ms, 4),
+           "algorithmic_flops_per_launch": res["flops_stage"][stage]}
+    if kern in TENSOR_KERNELS:
+        pk = measured_peaks()
+        peak = pk["bf16_tflops"] / 2.0
+        out.update(bound="tensor", peak=round(peak, 1),
+                   peak_source=f"dense TF32 = measured BF16 burst / 2 ({pk['source']}); "
+                               "the kernel issues three TF32 passes per product")
+    else:
+        peak = PEAK_TFLOPS[prec]
+        out.update(peak=round(peak, 3),
+                   peak_source=("derived: 152 SMs x 2.07 GHz x 256 flop/clk/SM (FP32 FMA)" if prec == "fp32"
+                                else "nominal GB300 FP64 rate 1.25 TFLOP/s"))
+    out["frac"] = round(achieved / peak, 4)
+    out["peak_fma_probe"] = round(fma_tflops, 3) if fma_tflops else None
+    out["frac_of_fma_probe"] = round(achieved / fma_tflops, 4) if fma_tflops else None
+    return out
 
 
 def e2e(ctx, res, steps, warmup):
@@ -864,6 +880,8 @@ def main():
         "gpu_launches": r32["launches"],
         "stage_ms": {k: round(v, 4) for k, v in r32["stage_ms"].items()},
         "stage_kernels": r32["kernels"],
+        "stage_tuning_ms": r32["tune"] and {st: {k: round(v, 3) for k, v in tab.items()}
+                                            for st, tab in r32["tune"].items()},
         "t_mirrored": r32["t_mirrored"],
         "fma_probe_tflops": {k: round(v, 3) for k, v in fma.items()},
         "setup": dict(r32["setup"], note="patterns, plans and tables (system_s) and the autotuner "
@@ -878,7 +896,9 @@ def main():
                         "gflops": round(r64["flops"] / (r64["ms_per_step"] * 1e-3) / 1e9, 1),
                         "roofline": roofline(r64, fma["fp64"]), "gpu_launches": r64["launches"],
                         "stage_ms": {k: round(v, 4) for k, v in r64["stage_ms"].items()},
-                        "stage_kernels": r64["kernels"], "t_mirrored": r64["t_mirrored"]}
+                        "stage_kernels": r64["kernels"], "t_mirrored": r64["t_mirrored"],
+                        "stage_tuning_ms": r64["tune"] and {st: {k: round(v, 3) for k, v in tab.items()}
+                                                            for st, tab in r64["tune"].items()}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, errs, _ = cpu_baseline(w, [r for r in (r32, r64) if r is not None])
         line["cpu_baseline"] = base
