@@ -198,16 +198,21 @@ lnv_status lnv_plan_product(lnv_ctx *ctx, const lnv_pattern *A, const lnv_patter
  * the k's at which one of the tile's columns holds op(B)_kj, for the tables
  * that are sparse as a whole but dense per tile (T = SX, U = SY); either
  * op(B); a symmetric first output is formed on the tiles of its upper part
- * and mirrored; FP32 values with NSF = 4 (other cases run kernel 0).
- * Kernels 9-11 need value arrays 16-byte aligned (else LNV_ERR_UNSUPPORTED
+ * and mirrored; FP32 values with NSF = 4 (other cases run kernel 0), 12
+ * and 13 the single-pass forms of 9 and 11: operands rounded to TF32 (round
+ * to nearest), one MMA per K step, FP32 accumulation, no low parts; their
+ * error (about 1e-4 relative) misses the FP32-level bound, so the
+ * autotuner never picks them: they measure the precision trade-off.
+ * Kernels 9-13 need value arrays 16-byte aligned (else LNV_ERR_UNSUPPORTED
  * from the multiply).
  * The default is 3 when at least half of the table's candidates hit, else 4,
  * when the tables fit a third of the free device memory. */
 lnv_status lnv_plan_info(const lnv_plan *plan, int64_t *triples, int *mode);
 /* Number of product kernels (0 .. LNV_NUM_KERNELS - 1). */
-#define LNV_NUM_KERNELS 12
-/* Select the kernel of a plan (0..11 as above); all give the same result up
- * to rounding order.  Kernels 3-11 build their tables on first selection
+#define LNV_NUM_KERNELS 14
+/* Select the kernel of a plan (0..13 as above); 0-11 give the same result up
+ * to rounding order (12 and 13 to single-pass TF32 accuracy).  Kernels 3-13
+ * build their tables on first selection
  * (allocates, synchronises).  LNV_ERR_UNSUPPORTED if the kernel cannot run
  * this plan. */
 lnv_status lnv_plan_set_kernel(lnv_ctx *ctx, lnv_plan *plan, int kernel);

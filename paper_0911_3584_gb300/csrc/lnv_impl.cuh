@@ -186,7 +186,8 @@ struct lnv_plan {
     // listed triples per output block, 8 kernel 5 with warp slices of half
     // the width, 9 8-row groups on the tcgen05 tensor cores (tables in tc),
     // 10 its NSF = 9 form, 11 tcgen05 tiles of 32 columns over their own k
-    // lists (tables in tc and tt)
+    // lists (tables in tc and tt), 12 and 13 the single-pass TF32 forms of 9
+    // and 11
     int mode;
     GroupPlan grp;
     GroupPlan tc;  // 8-row groups of the tensor-core kernels (9, 11; 7-row groups for 10)
@@ -247,7 +248,9 @@ lnv_status group_plan_build_into(lnv_ctx *ctx, lnv_plan *pl, int G, size_t budge
                                  GroupPlan &gp);
 // Kernel 9 (umma.cu): C = mask(op(A) B^T) on 8-row groups, tcgen05 tensor
 // cores, FP32 values, NSF = 4.
-lnv_status launch_umma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B, void *C);
+// onepass: kernel 12, the single-pass TF32 form (below the FP32-level bound).
+lnv_status launch_umma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B, void *C,
+                       bool onepass = false);
 // Finish kernel 9's or 10's tables after they are built (op(A) positions for A^T).
 lnv_status umma_prepare(lnv_ctx *ctx, lnv_plan *pl);
 // Kernel 10 (umma9.cu): C = mask(op(A) op(B)) on 7-row groups, tcgen05 tensor
@@ -257,8 +260,9 @@ lnv_status launch_umma9(lnv_ctx *ctx, const lnv_plan *pl, bool ta, bool tb, cons
 // 8-row groups over each tile's own k list, tcgen05 tensor cores, FP32
 // values, NSF = 4, either op(B).  upper: only the tiles holding a column j >=
 // the group's first row (a symmetric output formed on its upper triangle).
+// onepass: kernel 13, the single-pass TF32 form (below the FP32-level bound).
 lnv_status launch_umma_tile(lnv_ctx *ctx, const lnv_plan *pl, bool ta, bool tb, bool upper, const void *A,
-                            const void *B, void *C);
+                            const void *B, void *C, bool onepass = false);
 // Build kernel 11's tile plan from the plan's 8-row tables (tc, finished by
 // umma_prepare); LNV_ERR_UNSUPPORTED over the budget.
 lnv_status tile_plan_build(lnv_ctx *ctx, lnv_plan *pl, size_t budget_bytes);

@@ -274,7 +274,7 @@ lnv_status plan_pull_items(lnv_plan *pl)
 
 lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
 {
-    LNV_ARG(pl && kernel >= 0 && kernel < LNV_NUM_KERNELS, "kernel must be 0..11");
+    LNV_ARG(pl && kernel >= 0 && kernel < LNV_NUM_KERNELS, "kernel must be 0..13");
     if (kernel == 2) {
         if (!pl->B->symmetric) {
             set_error("the merge-join pull needs a symmetric B pattern");
@@ -282,11 +282,11 @@ lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
         }
         LNV_TRY(plan_pull_items(pl));
     }
-    if (kernel == 9) {
+    if (kernel == 9 || kernel == 12) {
         // 8-row group tables with the dense position table; the kernel reads
         // op(B) = B^T only (rows of the stored B_jk)
         if (!pl->trans_b) {
-            set_error("kernel 9 needs a product with op(B) = B^T");
+            set_error("kernels 9 and 12 need a product with op(B) = B^T");
             return LNV_ERR_UNSUPPORTED;
         }
         size_t free_b = 0, total_b = 0;
@@ -300,7 +300,7 @@ lnv_status plan_set_kernel(lnv_ctx *ctx, lnv_plan *pl, int kernel)
         tile_plan_free(&pl->tt);
         LNV_TRY(group_plan_build_into(ctx, pl, kTc9G, free_b / 3, true, false, pl->tc));
         LNV_TRY(umma_prepare(ctx, pl));
-    } else if (kernel == 11) {
+    } else if (kernel == 11 || kernel == 13) {
         // kernel 9's 8-row tables (either op(B)), then each 32-column tile's k list
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
@@ -339,8 +339,8 @@ lnv_status plan_set_split(lnv_ctx *ctx, lnv_plan *pl, int on)
 void plan_trim(lnv_plan *plan)
 {
     if (plan->mode != 7) triple_plan_free(&plan->tri);
-    if (plan->mode != 9 && plan->mode != 10 && plan->mode != 11) group_plan_free(&plan->tc);
-    if (plan->mode != 11) tile_plan_free(&plan->tt);
+    if (plan->mode < 9) group_plan_free(&plan->tc);
+    if (plan->mode != 11 && plan->mode != 13) tile_plan_free(&plan->tt);
     GroupPlan &gp = plan->grp;
     const bool dense = plan->mode == 3 || plan->mode == 5 || plan->mode == 6 || plan->mode == 8,
                sparse = plan->mode == 4;

@@ -1642,12 +1642,12 @@ template <typename T, int NSF, bool TA, bool TB>
 lnv_status dispatch_mode(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B1,
                          const void *B2, void *C1, void *C2)
 {
-    if (pl->mode == 9) {
-        // tcgen05 tensor cores: one product, FP32 values, NSF = 4, op(B) = B^T;
-        // other cases run the push kernel, which needs no tables
+    if (pl->mode == 9 || pl->mode == 12) {
+        // tcgen05 tensor cores: one product, FP32 values, NSF = 4, op(B) = B^T
+        // (12: single pass); other cases run the push kernel, which needs no tables
         if constexpr (NSF == 4 && sizeof(T) == 4 && TB) {
-            LNV_TRY(launch_umma(ctx, pl, A, B1, C1));
-            if (B2) LNV_TRY(launch_umma(ctx, pl, A, B2, C2));
+            LNV_TRY(launch_umma(ctx, pl, A, B1, C1, pl->mode == 12));
+            if (B2) LNV_TRY(launch_umma(ctx, pl, A, B2, C2, pl->mode == 12));
             return LNV_OK;
         } else {
             if (B2) return launch_push2<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, pl->sym1 && pl->split);
@@ -1666,13 +1666,14 @@ lnv_status dispatch_mode(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const 
             return launch_push2<T, NSF, 1, TA, TB>(ctx, pl, A, B1, nullptr, C1, nullptr, pl->sym1 && pl->split);
         }
     }
-    if (pl->mode == 11) {
+    if (pl->mode == 11 || pl->mode == 13) {
         // tcgen05 tiles over their own k lists: FP32 values, NSF = 4, either
-        // transpose; a symmetric first output on the tiles of its upper part
-        // (mirrored by the caller); other cases run the push kernel
+        // transpose (13: single pass); a symmetric first output on the tiles of
+        // its upper part (mirrored by the caller); other cases run the push kernel
         if constexpr (NSF == 4 && sizeof(T) == 4) {
-            LNV_TRY(launch_umma_tile(ctx, pl, TA, TB, pl->sym1 && pl->split, A, B1, C1));
-            if (B2) LNV_TRY(launch_umma_tile(ctx, pl, TA, TB, false, A, B2, C2));
+            const bool one = pl->mode == 13;
+            LNV_TRY(launch_umma_tile(ctx, pl, TA, TB, pl->sym1 && pl->split, A, B1, C1, one));
+            if (B2) LNV_TRY(launch_umma_tile(ctx, pl, TA, TB, false, A, B2, C2, one));
             return LNV_OK;
         } else {
             if (B2) return launch_push2<T, NSF, 2, TA, TB>(ctx, pl, A, B1, B2, C1, C2, pl->sym1 && pl->split);

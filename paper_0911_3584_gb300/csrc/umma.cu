@@ -80,7 +80,10 @@ struct UmmaShape {
     static_assert((NS & (NS - 1)) == 0, "ring depth is a power of two");
 };
 
-template <int MT, int KA, int NS, int P, bool TA>
+// ONE: the single-pass form (kernel 12): operands rounded to TF32, one MMA
+// of N = 32 per K step (A_hi B_hi), no low parts.  Its error, about 1e-4
+// relative, misses the FP32-level bound; it exists to measure that trade-off.
+template <int MT, int KA, int NS, int P, bool TA, bool ONE = false>
 __global__ void __launch_bounds__(5 * MT * 32, 2)
 k_umma(const int2 *__restrict__ items, const int64_t *__restrict__ k_off, const int32_t *__restrict__ apos,
        const int64_t *__restrict__ j_off, const int32_t *__restrict__ j_list, const int32_t *__restrict__ cpos,
@@ -155,8 +158,12 @@ k_umma(const int2 *__restrict__ items, const int64_t *__restrict__ k_off, const 
                     tc::fence_after_sync();
 #pragma unroll
                     for (int q = 0; q < KA / 2; ++q) {
-                        tc::mma_tf32_ts(d, aa[s][q], bd[s][q], id1, (i | q) != 0);
-                        tc::mma_tf32_ts(d, aa[s][q] + ACOLS, bd[s][q], id2, 1u);
+                        if (ONE) {
+                            tc::mma_tf32_ts(d, aa[s][q], bd[s][q], id2, (i | q) != 0);
+                        } else {
+                            tc::mma_tf32_ts(d, aa[s][q], bd[s][q], id1, (i | q) != 0);
+                            tc::mma_tf32_ts(d, aa[s][q] + ACOLS, bd[s][q], id2, 1u);
+                        }
                     }
                     tc::commit(empty_bar(s));
                 }
@@ -244,12 +251,17 @@ k_umma(const int2 *__restrict__ items, const int64_t *__restrict__ k_off, const 
                 } else {
                     w = *reinterpret_cast<const float4 *>(src + aq * 16);
                 }
-                float4 h4, l4;
-                tc::split_tf32x2_trunc(w.x, w.y, h4.x, h4.y, l4.x, l4.y);
-                tc::split_tf32x2_trunc(w.z, w.w, h4.z, h4.w, l4.z, l4.w);
                 unsigned char *dst = smem + s * S::BSTAGE + akk * 1024 + (am >> 1) * 128 + ((am & 1) * 4 + ax) * 16;
-                *reinterpret_cast<float4 *>(dst) = h4;
-                *reinterpret_cast<float4 *>(dst + 4 * 128) = l4;
+                if (ONE) {
+                    *reinterpret_cast<float4 *>(dst) =
+                        make_float4(tc::tf32_rna(w.x), tc::tf32_rna(w.y), tc::tf32_rna(w.z), tc::tf32_rna(w.w));
+                } else {
+                    float4 h4, l4;
+                    tc::split_tf32x2_trunc(w.x, w.y, h4.x, h4.y, l4.x, l4.y);
+                    tc::split_tf32x2_trunc(w.z, w.w, h4.z, h4.w, l4.z, l4.w);
+                    *reinterpret_cast<float4 *>(dst) = h4;
+                    *reinterpret_cast<float4 *>(dst + 4 * 128) = l4;
+                }
                 tc::fence_async_smem();
             }
             tc::fence_after_sync();
@@ -260,6 +272,13 @@ k_umma(const int2 *__restrict__ items, const int64_t *__restrict__ k_off, const 
                 const float4 v0 = *reinterpret_cast<const float4 *>(grow + (2 * h) * 128 * 16);
                 const float4 v1 = *reinterpret_cast<const float4 *>(grow + (2 * h + 1) * 128 * 16);
                 float hi[8], lo[8];
+                if (ONE) {
+                    const float e[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) hi[u] = tc::tf32_rna(e[u]);
+                    tc::tmem_st8(acol + (uint32_t)(8 * h), hi);
+                    continue;
+                }
                 tc::split_tf32x2_trunc(v0.x, v0.y, hi[0], hi[1], lo[0], lo[1]);
                 tc::split_tf32x2_trunc(v0.z, v0.w, hi[2], hi[3], lo[2], lo[3]);
                 tc::split_tf32x2_trunc(v1.x, v1.y, hi[4], hi[5], lo[4], lo[5]);
@@ -320,7 +339,12 @@ k_umma(const int2 *__restrict__ items, const int64_t *__restrict__ k_off, const 
                 float dh[8], dl[8];
                 if (nst > 0) {
                     tc::tmem_ld8(lane_base + (uint32_t)(t * 64 + 8 * c), dh);
-                    tc::tmem_ld8(lane_base + (uint32_t)(t * 64 + 32 + 8 * c), dl);
+                    if (ONE) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) dl[e] = 0.f;
+                    } else {
+                        tc::tmem_ld8(lane_base + (uint32_t)(t * 64 + 32 + 8 * c), dl);
+                    }
                 } else {
 #pragma unroll
                     for (int e = 0; e < 8; ++e) dh[e] = dl[e] = 0.f;
@@ -379,7 +403,7 @@ using Shape = UmmaShape<kMT, kKA, kNS, kP>;
 
 }  // namespace
 
-lnv_status launch_umma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B, void *C)
+lnv_status launch_umma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const void *B, void *C, bool onepass)
 {
     const GroupPlan &gp = pl->tc;
     if (!pl->trans_b) {
@@ -396,7 +420,8 @@ lnv_status launch_umma(lnv_ctx *ctx, const lnv_plan *pl, const void *A, const vo
         return LNV_ERR_UNSUPPORTED;
     }
     const bool ta = pl->trans_a != 0;
-    auto kern = ta ? k_umma<kMT, kKA, kNS, kP, true> : k_umma<kMT, kKA, kNS, kP, false>;
+    auto kern = ta ? (onepass ? k_umma<kMT, kKA, kNS, kP, true, true> : k_umma<kMT, kKA, kNS, kP, true, false>)
+                   : (onepass ? k_umma<kMT, kKA, kNS, kP, false, true> : k_umma<kMT, kKA, kNS, kP, false, false>);
     LNV_CUDA(ensure_smem((const void *)kern, Shape::SMEM));
     kern<<<(unsigned)gp.n_items, Shape::THREADS, Shape::SMEM, ctx->stream>>>(
         gp.items, gp.k_off, gp.apos, gp.j_off, gp.j_list, gp.cpos, gp.bidx_off, gp.bidx, (const float *)A,

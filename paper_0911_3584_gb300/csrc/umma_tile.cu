@@ -69,7 +69,10 @@ static_assert(4 * (kSmem + 1024) <= 228 * 1024 && 5 * (kSmem + 1024) > 228 * 102
               "exactly four CTAs per SM");
 static_assert(kKA == 4 && kNPW * 32 == 4 * kCols, "a lane reads its four k offsets in one 8-byte load");
 
-template <bool TA, bool TB>
+// ONE: the single-pass form (kernel 13): operands rounded to TF32, one MMA of
+// N = 32 per K step, no low parts (about 1e-4 relative error: it misses the
+// FP32-level bound and is kept to measure that trade-off).
+template <bool TA, bool TB, bool ONE>
 __global__ void __launch_bounds__(kThreads, 4)
 k_umma_tile(const int32_t *__restrict__ sub, const int2 *__restrict__ items, const int64_t *__restrict__ ck_off,
             const int32_t *__restrict__ ck_brow, const int32_t *__restrict__ ck_apos,
@@ -140,8 +143,12 @@ k_umma_tile(const int32_t *__restrict__ sub, const int2 *__restrict__ items, con
                     tc::fence_after_sync();
 #pragma unroll
                     for (int q = 0; q < kKA / 2; ++q) {
-                        tc::mma_tf32_ts(tm, aa[s][q], bd[s][q], id1, (i | q) != 0);
-                        tc::mma_tf32_ts(tm, aa[s][q] + kACOLS, bd[s][q], id2, 1u);
+                        if (ONE) {
+                            tc::mma_tf32_ts(tm, aa[s][q], bd[s][q], id2, (i | q) != 0);
+                        } else {
+                            tc::mma_tf32_ts(tm, aa[s][q], bd[s][q], id1, (i | q) != 0);
+                            tc::mma_tf32_ts(tm, aa[s][q] + kACOLS, bd[s][q], id2, 1u);
+                        }
                     }
                     tc::commit(empty_bar(s));
                 }
@@ -226,12 +233,17 @@ k_umma_tile(const int32_t *__restrict__ sub, const int2 *__restrict__ items, con
                 } else {
                     w = *reinterpret_cast<const float4 *>(src + aq * 16);
                 }
-                float4 h4, l4;
-                tc::split_tf32x2_trunc(w.x, w.y, h4.x, h4.y, l4.x, l4.y);
-                tc::split_tf32x2_trunc(w.z, w.w, h4.z, h4.w, l4.z, l4.w);
                 unsigned char *dst = smem + s * kBSTAGE + akk * 1024 + (am >> 1) * 128 + ((am & 1) * 4 + ax) * 16;
-                *reinterpret_cast<float4 *>(dst) = h4;
-                *reinterpret_cast<float4 *>(dst + 4 * 128) = l4;
+                if (ONE) {
+                    *reinterpret_cast<float4 *>(dst) =
+                        make_float4(tc::tf32_rna(w.x), tc::tf32_rna(w.y), tc::tf32_rna(w.z), tc::tf32_rna(w.w));
+                } else {
+                    float4 h4, l4;
+                    tc::split_tf32x2_trunc(w.x, w.y, h4.x, h4.y, l4.x, l4.y);
+                    tc::split_tf32x2_trunc(w.z, w.w, h4.z, h4.w, l4.z, l4.w);
+                    *reinterpret_cast<float4 *>(dst) = h4;
+                    *reinterpret_cast<float4 *>(dst + 4 * 128) = l4;
+                }
                 tc::fence_async_smem();
             }
             tc::fence_after_sync();
@@ -253,6 +265,13 @@ k_umma_tile(const int32_t *__restrict__ sub, const int2 *__restrict__ items, con
                     }
                 }
                 float hi[8], lo[8];
+                if (ONE) {
+                    const float e[8] = {v[0].x, v[0].y, v[0].z, v[0].w, v[1].x, v[1].y, v[1].z, v[1].w};
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) hi[u] = tc::tf32_rna(e[u]);
+                    tc::tmem_st8(acol + (uint32_t)(8 * h), hi);
+                    continue;
+                }
                 tc::split_tf32x2_trunc(v[0].x, v[0].y, hi[0], hi[1], lo[0], lo[1]);
                 tc::split_tf32x2_trunc(v[0].z, v[0].w, hi[2], hi[3], lo[2], lo[3]);
                 tc::split_tf32x2_trunc(v[1].x, v[1].y, hi[4], hi[5], lo[4], lo[5]);
@@ -306,7 +325,12 @@ k_umma_tile(const int32_t *__restrict__ sub, const int2 *__restrict__ items, con
                 float dh[8], dl[8];
                 if (nst > 0) {
                     tc::tmem_ld8(lane_base + (uint32_t)(8 * c), dh);
-                    tc::tmem_ld8(lane_base + (uint32_t)(32 + 8 * c), dl);
+                    if (ONE) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) dl[e] = 0.f;
+                    } else {
+                        tc::tmem_ld8(lane_base + (uint32_t)(32 + 8 * c), dl);
+                    }
                 } else {
 #pragma unroll
                     for (int e = 0; e < 8; ++e) dh[e] = dl[e] = 0.f;
@@ -497,7 +521,7 @@ lnv_status tile_plan_build(lnv_ctx *ctx, lnv_plan *pl, size_t budget_bytes)
 }
 
 lnv_status launch_umma_tile(lnv_ctx *ctx, const lnv_plan *pl, bool ta, bool tb, bool upper, const void *A,
-                            const void *B, void *C)
+                            const void *B, void *C, bool onepass)
 {
     const GroupPlan &gp = pl->tc;
     const TilePlan &tt = pl->tt;
@@ -513,8 +537,10 @@ lnv_status launch_umma_tile(lnv_ctx *ctx, const lnv_plan *pl, bool ta, bool tb, 
     const bool sub = upper && pl->sym1;
     const int64_t n = sub ? tt.n_up : tt.n_items;
     if (n == 0) return LNV_OK;
-    auto kern = ta ? (tb ? k_umma_tile<true, true> : k_umma_tile<true, false>)
-                   : (tb ? k_umma_tile<false, true> : k_umma_tile<false, false>);
+    auto kern = onepass ? (ta ? (tb ? k_umma_tile<true, true, true> : k_umma_tile<true, false, true>)
+                              : (tb ? k_umma_tile<false, true, true> : k_umma_tile<false, false, true>))
+                        : (ta ? (tb ? k_umma_tile<true, true, false> : k_umma_tile<true, false, false>)
+                              : (tb ? k_umma_tile<false, true, false> : k_umma_tile<false, false, false>));
     LNV_CUDA(ensure_smem((const void *)kern, kSmem));
     kern<<<(unsigned)n, kThreads, kSmem, ctx->stream>>>(
         sub ? tt.up : nullptr, tt.items, tt.ck_off, tt.ck_brow, tt.ck_apos, tt.ck_tab, gp.j_off, gp.j_list, gp.cpos,

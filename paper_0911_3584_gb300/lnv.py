@@ -300,7 +300,7 @@ class Plan:
         self.triples, self.mode = t.value, self.KERNELS[m.value]
 
     KERNELS = ("push", "pull", "pull-merge", "group", "group-sparse", "group-pipe", "group-mma", "triples",
-               "group-pipe-half", "tensor", "tensor9", "tensor-tile")
+               "group-pipe-half", "tensor", "tensor9", "tensor-tile", "tensor-1pass", "tensor-tile-1pass")
 
     def set_kernel(self, kernel):
         k = self.KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)

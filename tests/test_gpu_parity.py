@@ -331,6 +331,54 @@ def test_tensor_tile_product_ragged_groups(ctx, n_atoms):
     assert ctx.device_status() == 0
 
 
+# single-pass TF32 (operands rounded to TF32, FP32 sums): unit roundoff 2^-11,
+# so products sit near 1e-4 relative and well below 3e-3; the FP32 bound of
+# 2e-5 is out of its reach (the emulation in test_oracle measures it)
+TOL_1PASS = 3e-3
+
+
+@pytest.mark.parametrize("kernel", ["tensor-1pass", "tensor-tile-1pass"])
+@pytest.mark.parametrize("n_atoms", [7, 33, 131])
+def test_single_pass_tensor_kernels(ctx, kernel, n_atoms):
+    """Kernels 12 and 13 (single-pass TF32 forms of 9 and 11) on ragged groups,
+    every transpose they take, against the FP64 oracle: within the TF32 bound,
+    and above the 3xTF32 kernels' error (they really run one pass)."""
+    rng = np.random.default_rng(300 + n_atoms)
+    cell = np.array([20.0, 20.0, 20.0])
+    pos = rng.uniform(0, 9.0, size=(n_atoms, 3))
+    ra, rb, rc = 4.0, 7.0, 6.0
+    PA, PB, PC = (Pattern.build(ctx, pos, cell, r) for r in (ra, rb, rc))
+    oa, ob, oc = (oracle.pattern(pos, cell, r) for r in (ra, rb, rc))
+    A = rounded(oracle.csr(*oa, rng.standard_normal((oa[1].size, 4, 4))), torch.float32)
+    B = rounded(oracle.csr(*ob, rng.standard_normal((ob[1].size, 4, 4))), torch.float32)
+    for ta in (False, True):
+        for tb in ((True,) if kernel == "tensor-1pass" else (False, True)):
+            plan = Plan(ctx, PA, PB, PC, trans_a=ta, trans_b=tb)
+            ref = oracle.mprod(oracle.transpose(A) if ta else A, oracle.transpose(B) if tb else B, oc)
+            Ad, Bd = to_dev(A["val"], torch.float32, ctx.device), to_dev(B["val"], torch.float32, ctx.device)
+            plan.set_kernel(kernel)
+            e1 = rel_fro(plan.multiply(Ad, Bd).cpu().numpy(), ref["val"])
+            plan.set_kernel(kernel.replace("-1pass", ""))
+            e3 = rel_fro(plan.multiply(Ad, Bd).cpu().numpy(), ref["val"])
+            assert e1 <= TOL_1PASS, (ta, tb, e1)
+            assert e3 <= TOL[torch.float32][0] and e1 > 4 * e3, (ta, tb, e1, e3)
+    assert ctx.device_status() == 0
+
+
+def test_lnv_512_atoms_single_pass_products(ctx, si512):
+    """The FP32 evaluation with Z, W on kernel 12 and TU, Q on kernel 13: E,
+    N_e and G within the single-pass TF32 bound of the FP64 oracle."""
+    w, ref = si512
+    sysm = System(ctx, 4, "fp32", w["pos"], w["cell"], 6.6, 8.0)
+    for st, k in dict(TU="tensor-tile-1pass", Z="tensor-1pass", Q="tensor-tile-1pass", W="tensor-1pass").items():
+        sysm.set_stage_kernel(st, k)
+    _, out, (G, _) = _gpu_lnv(ctx, w, torch.float32, sysm=sysm)
+    assert abs(out[0, 0] - ref["E"]) <= TOL_1PASS * abs(ref["E"])
+    assert abs(out[0, 1] - ref["Ne"]) <= TOL_1PASS * abs(ref["Ne"])
+    assert rel_fro(G, ref["G"]) <= TOL_1PASS
+    assert ctx.device_status() == 0
+
+
 def test_tensor_tile_repeated_calls_are_identical(ctx):
     """Kernel 11 sums in a fixed order: two launches of T = S X (op(B) = B)
     give bit-identical output, within the FP32 bound of the oracle."""
