@@ -51,3 +51,39 @@ def test_traffic_only_for_the_recorded_sources(monkeypatch):
         assert got is None
     monkeypatch.setattr(bench, "product_source_sha", lambda: "000000000000")
     assert bench.ncu_traffic("TU", "fp32") is None
+
+
+def test_roofline_of_a_tensor_core_stage():
+    """A dominant stage on a tcgen05 kernel is reported against the dense
+    TF32 peak (half the measured BF16 burst), with the FMA probe beside it."""
+    res = _res()
+    res["kernels"]["TU"] = "tensor-tile"
+    r = bench.roofline(res, fma_tflops=76.0)
+    tf32 = bench.measured_peaks()["bf16_tflops"] / 2.0
+    assert r["bound"] == "tensor" and r["stage"] == "TU"
+    assert abs(r["peak"] - round(tf32, 1)) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / tf32) < 1e-3
+    assert abs(r["frac_of_fma_probe"] - r["achieved"] / 76.0) < 1e-3
+    assert r["kernel"].startswith("k_umma_tile") and "k_mirror_lower" in r["kernel"]
+    # the same stage on a SIMT kernel stays bound by the FMA pipe
+    res["kernels"]["TU"] = "group-pipe"
+    assert bench.roofline(res, fma_tflops=76.0)["bound"] == "alu"
+
+
+def test_tensor_stage_list_and_single_pass_pins():
+    """roofline_tensor lists exactly the tcgen05 stages; the single-pass
+    measurement pins kernels 12 and 13 where 9 and 11 run, and names only
+    kernels the binding knows."""
+    from paper_0911_3584_gb300.lnv import Plan
+
+    res = _res()
+    res["kernels"].update({"TU": "tensor-tile", "Z": "tensor", "W": "tensor-1pass"})
+    got = {t["stage"] for t in bench.roofline_tensor(res)}
+    assert got == {"TU", "Z", "W"}
+    pins = bench.SINGLE_PASS_KERNELS
+    assert pins["mirror"] == "1"
+    for st, k in pins.items():
+        if st != "mirror":
+            assert k in Plan.KERNELS and k in bench.KERNEL_NAME
+    assert {pins[s] for s in ("Z", "W")} == {"tensor-1pass"}
+    assert {pins[s] for s in ("TU", "Q")} == {"tensor-tile-1pass"}
