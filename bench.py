@@ -260,8 +260,9 @@ def time_path(ctx, w, prec, steps, warmup, dist, kernels=None):
 
 
 def measured_peaks():
-    """The machine's measured peaks (generated MEASURED_PEAKS.json at the repo
-    root), or the profiling recipe's fallback figures."""
+    """The GPU's measured copy bandwidth and BF16 GEMM rate (MEASURED_PEAKS.json
+    at the repository root), else fallback figures of 6.8 TB/s and 1.9
+    PFLOP/s from an earlier measurement."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:

@@ -21,7 +21,7 @@ partitions and bundles; Sec. 3, scaling studies).  Two forms are provided:
 The distribution logic here is independent of where the local products run:
 ``lnv_partitioned`` takes the local product and trace as callables on
 block-CSR dicts ({"rp", "col", "val"}, full-size, valid on the rows the rank
-holds), so the same driver runs on CPU ranks (the tests) or around a GPU
+holds), so the same code runs on CPU ranks (the tests) or around a GPU
 product.
 """
 from __future__ import annotations
