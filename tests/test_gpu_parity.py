@@ -907,6 +907,51 @@ def test_graph_captured_batched_evaluation(ctx, dtype):
     assert lb == G_dev.shape[0]
 
 
+@pytest.mark.parametrize("kernels", [
+    dict(XY="triples", TU="tensor-tile", Z="tensor", Q="tensor-tile", W="tensor"),
+    dict(XY="triples", TU="tensor-tile-1pass", Z="tensor-1pass", Q="tensor-tile-1pass", W="tensor-1pass")])
+def test_graph_captured_tensor_core_kernels(ctx, kernels):
+    """The batched FP32 evaluation with the tcgen05 kernels pinned (the bench's
+    choice, and its single-pass form) captured in a CUDA graph: replays equal
+    direct evaluations bit for bit after L changes in place, and every system
+    stays within its bound of the oracle (FP32, or single-pass TF32)."""
+    sizes = [3, 2, 4]
+    ws = [workload(n, 4, 6.6, 8.0, seed=2000 + k)[0] for k, n in enumerate(sizes)]
+    off = [0]
+    for w in ws:
+        off.append(off[-1] + w["pos"].shape[0])
+    sysb = System(ctx, 4, "fp32", np.concatenate([w["pos"] for w in ws]), [w["cell"] for w in ws],
+                  6.6, 8.0, seg_off=off)
+    for st, k in kernels.items():
+        sysb.set_stage_kernel(st, k)
+    assert sysb.stage_kernels() == kernels
+    cat = {k: to_dev(np.concatenate([w[k] for w in ws]), torch.float32, ctx.device) for k in ("S", "H", "L")}
+    graph, out_g, G_g = sysb.capture(cat["S"], cat["H"], cat["L"])
+    for scale in (1.0, 0.9):
+        cat["L"].mul_(scale)
+        graph.replay()
+        torch.cuda.synchronize()
+        out_d, G_d = sysb.energy_grad(cat["S"], cat["H"], cat["L"])
+        assert torch.equal(out_g, out_d) and torch.equal(G_g, G_d)
+    assert ctx.device_status() == 0
+    one = kernels["Z"].endswith("1pass")
+    tm, ts = (TOL_1PASS, TOL_1PASS) if one else TOL[torch.float32]
+    L_dev = cat["L"].double().cpu().numpy()
+    G_dev = G_g.double().cpu().numpy()
+    lb = 0
+    for k, w in enumerate(ws):
+        nl = w["l_col"].size
+        ref = oracle.lnv_energy_grad(w["pos"], w["cell"], 6.6, 8.0,
+                                     rounded(oracle.csr(w["sh_row_ptr"], w["sh_col"], w["S"]), torch.float32),
+                                     rounded(oracle.csr(w["sh_row_ptr"], w["sh_col"], w["H"]), torch.float32),
+                                     oracle.csr(w["l_row_ptr"], w["l_col"], L_dev[lb:lb + nl]))
+        o = out_g[k].cpu().numpy()
+        assert abs(o[0] - ref["E"]) <= ts * abs(ref["E"]), (k, o[0], ref["E"])
+        assert abs(o[1] - ref["Ne"]) <= ts * abs(ref["Ne"]), (k, o[1], ref["Ne"])
+        assert rel_fro(G_dev[lb:lb + nl], ref["G"]) <= tm, k
+        lb += nl
+
+
 # ------------------------------------------------------------------ minimisation (next row)
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
